@@ -1,0 +1,132 @@
+// vp_internal.cuh -- context and device helpers shared by the CUDA sources of
+// the GB300 Vlasov--Poisson library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/vp.h"
+
+#define VP_CUDA_TRY(expr)                                        \
+    do {                                                         \
+        cudaError_t _e = (expr);                                 \
+        if (_e != cudaSuccess) {                                 \
+            vp_note_cuda_error(_e, #expr, __FILE__, __LINE__);   \
+            return VP_ERR_CUDA;                                  \
+        }                                                        \
+    } while (0)
+
+void vp_note_cuda_error(cudaError_t e, const char *expr, const char *file, int line);
+
+// One advection line's shift alpha = u tau / h written as |alpha| = s + beta
+// with the direction of travel.  The PFC partial-flux weights of Sec. 2.1
+// (third-order reconstruction): c0 = beta, c1 = beta(1-beta)(2-beta)/6,
+// c2 = beta(1-beta)(1+beta)/6.  code = 2 s + (alpha < 0).
+template <typename T>
+struct __align__(16) LineCoef {
+    int code;
+    T c0, c1, c2;
+};
+
+// Device-resident scalars of a context.
+struct DevScalars {
+    double dt;          // dt of the current step
+    double t;           // simulated time
+    double lost;        // phase-space sum of f that left (unscaled)
+    double amax;        // max_l,x |g_l| / dv_l of the last dt evaluation
+    double pad[4];
+};
+
+struct FFTAxis {
+    int n;              // length
+    int nrad;           // number of radix stages
+    int rad[24];        // radices, applied in order
+    double2 *tw;        // twiddles W_n^k = exp(-2 pi i k / n), k < n (device)
+};
+
+struct vp_ctx {
+    vp_config cfg;
+    int device;
+    cudaStream_t stream;        // caller's stream
+    cudaStream_t cap;           // internal stream used to capture graphs
+    void *f;                    // borrowed distribution function
+    int isdouble;
+    size_t esize;
+    int n[3], nv[3];
+    long long np, nvc, ncells;  // spatial cells, velocity cells, total
+    double dx[3], dv[3];
+    double dvol_x, dvol_v;
+    int periodic_space;
+    int isolated;
+
+    // fields (device, owned)
+    double *rho;                // np
+    double *phi;                // nfft (real potential on the FFT grid)
+    double *g;                  // 3 np
+    double2 *cbuf;              // nfft complex work buffer
+    double *ghat;               // nfft real Green's function in k space / nfft
+    int fn[3];                  // FFT grid (n or 2n)
+    long long nfft;
+    FFTAxis ax[3];
+
+    // tables (device, owned)
+    void *coef_kick1;           // LineCoef<T>[np][3] for the first half kick
+    void *coef_kick2;           // LineCoef<T>[np][3] for the second half kick
+    void *coef_drift;           // LineCoef<T>[3][maxnv]
+    int maxnv;
+    double *vc[3];              // velocity cell centres (device)
+    double *red;                // reduction scratch (2 np + 64 doubles)
+    double *rho2;               // density of the current f for diagnostics
+    DevScalars *sc;             // device scalars
+    DevScalars *sc_host;        // pinned mirror for read-back
+
+    // CUDA graphs (built lazily) and their kernel-node counts
+    cudaGraphExec_t g_first, g_middle, g_last, g_single;
+    int graphs_ready;
+    long long nk_first, nk_middle, nk_last;
+    long long kernels_launched;
+
+    // adjoint scratch (lazily allocated)
+    void *adj_f;                // one state in f's dtype
+    double *adj_g;              // 3 np
+    double *adj_lg;             // 3 np
+    double *adj_tmp;            // nfft
+    void **adj_states;          // nine sweep inputs (f's dtype)
+    int adj_nstates;
+};
+
+// ---------------------------------------------------------------------------
+// launch wrappers implemented in the .cu files; all return cudaError_t of the
+// launch (cudaGetLastError)
+// ---------------------------------------------------------------------------
+cudaError_t launch_coef_drift(vp_ctx *c, const double *tau_ptr, double factor, void *out);
+cudaError_t launch_coef_kick(vp_ctx *c, const double *g, const double *tau_ptr, double factor,
+                             void *out);
+cudaError_t launch_dt(vp_ctx *c, const double *g);
+cudaError_t launch_advance_time(vp_ctx *c);
+cudaError_t launch_drift(vp_ctx *c, void *f, int axis, const void *coef);
+// nsweeps velocity sweeps over every cube; sweep k runs along axis
+// (first_axis + k) % 3 with table coef_a for k < 3 and coef_b afterwards
+cudaError_t launch_kick(vp_ctx *c, void *f, const void *coef_a, const void *coef_b, int nsweeps,
+                        int first_axis);
+cudaError_t launch_density(vp_ctx *c, const void *f, double *rho);
+cudaError_t launch_field_solve(vp_ctx *c, const double *rho, double *g_out);
+cudaError_t launch_energy_partials(vp_ctx *c, const void *f, double *partials);
+cudaError_t launch_copy_phi_box(vp_ctx *c, double *dst);
+cudaError_t launch_dot_rho_phi(vp_ctx *c, const double *rho, double *out2);
+cudaError_t launch_reduce_strided(vp_ctx *c, const double *in, long long n, int stride,
+                                  double *out);
+int vp_sm_count();
+
+int vp_fft_plan_axis(FFTAxis *a, int n);
+cudaError_t launch_fft(vp_ctx *c, double2 *data, int axis, int inverse);
+
+// adjoint
+cudaError_t launch_drift_adjoint(vp_ctx *c, const void *fin, double *lam, int axis,
+                                 const void *coef);
+cudaError_t launch_kick_adjoint(vp_ctx *c, const void *fin, double *lam, int vaxis,
+                                const void *coef, const double *g, double tau_factor,
+                                double *lam_g);
+cudaError_t launch_field_adjoint(vp_ctx *c, const double *lam_g, double *lam_f);
+cudaError_t launch_functional(vp_ctx *c, int kind, const double *rho, const double *target,
+                              double *lam_f);

@@ -1,0 +1,251 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs, element by element.
+
+Tolerances (derived from the arithmetic):
+  * FP64 storage: both sides do the same algebra in a different order
+    (oracle: ratio-form corrector and face sums; GPU: clamp form and the
+    telescoped update), so cells agree to a few ulps: max |diff| <= 1e-12 max f
+    per sweep and relative L1 <= 1e-11 after a few steps.
+  * FP32 storage: one rounding of f per sweep (relative 6e-8) plus FP32
+    weights: relative L1 <= 2e-6 per sweep, and the 20-step bound 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytestmark = pytest.mark.skip(reason="needs a CUDA GPU")
+
+from oracle import vp_oracle as O  # noqa: E402
+from paper_1206_6152_gb300 import inputs as I  # noqa: E402
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1206_6152_gb300 import build as B
+    B.build()
+
+
+def gpu_sim(w, f_np, dtype=None):
+    from paper_1206_6152_gb300.vlasov import VlasovPoisson, config_of
+    tdt = dtype or (torch.float32 if w.dtype == "f32" else torch.float64)
+    f = torch.from_numpy(np.ascontiguousarray(f_np)).to(DEV, tdt)
+    return VlasovPoisson(config_of(w, tdt), f), f
+
+
+def rel_l1(a, b):
+    return float(np.abs(a - b).sum() / np.abs(b).sum())
+
+
+SMALL = [
+    dict(n=(8, 6, 5), nv=(12, 10, 9)),
+    dict(n=(7, 1, 3), nv=(5, 8, 1)),
+    dict(n=(4, 4, 4), nv=(16, 16, 16)),
+]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("shape", SMALL)
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("space_bc", ["periodic", "outflow"])
+def test_each_sweep_matches_oracle(shape, dtype, space_bc):
+    w = I.small_maxwell(dtype=dtype, space_bc=space_bc, amp=0.3, **shape)
+    grid = O.Grid.of(w)
+    rng = np.random.default_rng(11)
+    f0 = I.initial_condition(w) * (1 + 0.3 * rng.random(w.shape)).astype(
+        np.float32 if dtype == "f32" else np.float64)
+    acc = rng.normal(size=(3,) + w.n) * 4.0
+    sim, f = gpu_sim(w, f0)
+    tol_max = 1e-12 if dtype == "f64" else 2e-6
+    per = space_bc == "periodic"
+    # taus: sub-cell, multi-cell and negative shifts
+    for axis in range(6):
+        for tau in (0.013, -0.021, 0.37, -0.9):
+            f.copy_(torch.from_numpy(f0))
+            sim.set_accel(torch.from_numpy(acc))
+            sim.sweep(axis, tau)
+            got = f.cpu().numpy().astype(np.float64)
+            ref = f0.astype(np.float64).copy()
+            if axis < 3:
+                O.sweep(ref, axis, grid.vc(axis), tau, grid.dx[axis], per)
+            else:
+                O.sweep(ref, axis, acc[axis - 3], tau, grid.dv[axis - 3], False)
+            err = np.abs(got - ref).max() / ref.max()
+            assert err <= tol_max, (axis, tau, err)
+            assert got.min() >= 0.0
+    sim.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_integer_courant_drift_is_exact(dtype):
+    w = I.small_maxwell(n=(6, 5, 4), nv=(4, 6, 2), dtype=dtype, G=0.0)
+    w = w.replace(vlo=(-2.0, -3.0, -1.0), vhi=(2.0, 3.0, 1.0))
+    grid = O.Grid.of(w)
+    rng = np.random.default_rng(1)
+    f0 = rng.random(w.shape).astype(np.float32 if dtype == "f32" else np.float64)
+    sim, f = gpu_sim(w, f0)
+    for a in range(3):
+        f.copy_(torch.from_numpy(f0))
+        sim.sweep(a, 2 * grid.dx[a] / grid.dv[a])     # v_j dt / dx = 2j + 1 - Nv
+        got = f.cpu().numpy()
+        expect = np.empty_like(f0)
+        for j in range(w.nv[a]):
+            sl = [slice(None)] * 6
+            sl[3 + a] = j
+            expect[tuple(sl)] = np.roll(f0[tuple(sl)], 2 * j + 1 - w.nv[a], axis=a)
+        assert np.array_equal(got, expect)                 # bitwise
+    sim.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_density_and_field_match_oracle(dtype):
+    for bc in ("periodic", "isolated"):
+        w = I.small_maxwell(n=(8, 6, 10), nv=(6, 5, 7), dtype=dtype, amp=0.4,
+                            poisson_bc=bc)
+        if bc == "isolated":
+            w = w.replace(box_lo=(-0.4, -0.3, -0.5), box_hi=(0.4, 0.3, 0.5),
+                          space_bc="outflow")
+        grid = O.Grid.of(w)
+        f0 = I.initial_condition(w)
+        sim, f = gpu_sim(w, f0)
+        rho_g = sim.density().cpu().numpy()
+        rho_o = O.density(f0.astype(np.float64), grid)
+        assert np.abs(rho_g - rho_o).max() <= 1e-14 * rho_o.max()
+        _, phi_g, g_g = (t.cpu().numpy() for t in sim.field())
+        ghat = np.fft.fftn(O.green_isolated(grid, w.G)) if bc == "isolated" else None
+        phi_o = O.poisson(rho_o, grid, w.G, bc, ghat)
+        g_o = O.force(phi_o, grid, bc)
+        assert np.abs(phi_g - O.potential_in_box(phi_o, grid)).max() <= 1e-12 * np.abs(phi_o).max()
+        assert np.abs(g_g - g_o).max() <= 1e-11 * np.abs(g_o).max()
+        sim.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-11), ("f32", 1e-5)])
+@pytest.mark.parametrize("bc", ["periodic", "isolated"])
+def test_split_steps_match_oracle(dtype, tol, bc):
+    w = I.small_maxwell(n=(8, 6, 5), nv=(12, 10, 9), dtype=dtype, amp=0.3, G=25.0)
+    if bc == "isolated":
+        w = w.replace(box_lo=(-0.4, -0.3, -0.25), box_hi=(0.4, 0.3, 0.25), poisson_bc="isolated",
+                      space_bc="outflow")
+    f0 = I.initial_condition(w)
+    sim, f = gpu_sim(w, f0)
+    e0 = sim.energy()
+    t = sim.step(4, sync=True)
+    got = f.cpu().numpy().astype(np.float64)
+    e1 = sim.energy()
+    ref = O.Simulation(f0, O.Grid.of(w), O.Params.of(w))
+    r0 = ref.energy()
+    ref.step(4)
+    r1 = ref.energy()
+    assert abs(t - ref.t) <= 1e-13 * ref.t
+    assert rel_l1(got, ref.f) <= tol
+    assert got.min() >= 0.0
+    for k, name in enumerate(["M", "K", "U", "E", "M_out"]):
+        scale = abs(r0[0]) if name in ("M", "M_out") else max(abs(r0[1]), abs(r0[2]))
+        assert abs(e1[name] - r1[k]) <= 10 * tol * scale, name
+        if name != "M_out":
+            assert abs(e0[name] - r0[k]) <= 1e-12 * scale, name
+    sim.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_landau_16_20_steps(dtype):
+    """The 16^3 x 16^3 Landau-damping workload, 20 steps: relative L1(f) vs
+    the FP64 oracle <= 1e-5, mass drift <= 1e-7, f >= 0."""
+    w = I.landau_c1()
+    f0 = I.initial_condition(w, np.float64)
+    sim, f = gpu_sim(w, f0.astype(np.float32) if dtype == "f32" else f0,
+                     torch.float32 if dtype == "f32" else torch.float64)
+    M0 = sim.energy()["M"]
+    sim.step(w.steps)
+    got = f.cpu().numpy().astype(np.float64)
+    e = sim.energy()
+    ref = O.Simulation(f0, O.Grid.of(w), O.Params.of(w))
+    ref.step(w.steps)
+    err = rel_l1(got, ref.f)
+    assert err <= (1e-11 if dtype == "f64" else 1e-5), err
+    assert abs(e["M"] + e["M_out"] - M0) <= 1e-7 * M0
+    rM = ref.energy()
+    assert abs(e["M"] - rM[0]) <= 1e-7 * M0
+    assert got.min() >= 0.0
+    sim.close()
+
+
+@pytest.mark.gpu
+def test_host_buffer_entry_point_matches_device_path():
+    w = I.small_maxwell(n=(8, 6, 5), nv=(12, 10, 9), dtype="f32", amp=0.3, G=25.0)
+    f0 = I.initial_condition(w)
+    sim, f = gpu_sim(w, f0)
+    sim.step(3)
+    dev_result = f.cpu().numpy()
+    host_in = torch.from_numpy(f0).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    t, diag = sim.step_host(host_in, 3, host_out, diagnostics=True)
+    assert np.array_equal(host_out.numpy(), dev_result)
+    e = sim.energy()
+    assert diag[0] == pytest.approx(e["M"], rel=1e-14)
+    sim.close()
+
+
+@pytest.mark.gpu
+def test_degenerate_inputs():
+    # all-zero f: stays zero, no NaN; single-cell axes; outflow everywhere
+    w = I.small_maxwell(n=(1, 3, 1), nv=(1, 4, 3), dtype="f32", space_bc="outflow")
+    sim, f = gpu_sim(w, np.zeros(w.shape, np.float32))
+    sim.step(2)
+    assert torch.count_nonzero(f).item() == 0
+    e = sim.energy()
+    assert e["M"] == 0.0 and math.isfinite(e["E"])
+    sim.close()
+
+
+@pytest.mark.gpu
+def test_error_codes():
+    from paper_1206_6152_gb300._lib import VPError
+    w = I.small_maxwell(dtype="f64")
+    sim, f = gpu_sim(w, I.initial_condition(w))
+    with pytest.raises(VPError) as ei:
+        sim.sweep(7, 0.1)
+    assert ei.value.code == -5
+    with pytest.raises(VPError):
+        sim.step(-1)
+    sim.close()
+    # isolated Poisson needs cubic cells
+    from paper_1206_6152_gb300.vlasov import VlasovPoisson, config_of
+    w2 = w.replace(poisson_bc="isolated")
+    with pytest.raises(VPError) as ei:
+        VlasovPoisson(config_of(w2), torch.zeros(w2.shape, dtype=torch.float64, device=DEV))
+    assert ei.value.code == -1
+
+
+@pytest.mark.gpu
+@pytest.mark.slow
+def test_jeans_32_full_size_two_steps():
+    """The 32^3 x 32^3 FP32 Jeans workload at full size, in the launch
+    configuration the benchmark times (prologue, fused 6-sweep body, tail),
+    against the oracle for two steps."""
+    w = I.jeans_c2()
+    f0 = I.initial_condition(w)                 # float32, 4.3 GB
+    sim, f = gpu_sim(w, f0)
+    M0 = sim.energy()["M"]
+    sim.step(2)
+    e = sim.energy()
+    got = f.cpu().numpy()
+    sim.close()
+    del f
+    ref = O.Simulation(f0.astype(np.float64), O.Grid.of(w), O.Params.of(w))
+    del f0
+    ref.step(2)
+    diff = np.abs(got.astype(np.float64) - ref.f)
+    assert diff.sum() / np.abs(ref.f).sum() <= 2e-6
+    assert diff.max() <= 1e-5 * ref.f.max()
+    assert got.min() >= 0.0
+    assert abs(e["M"] + e["M_out"] - M0) <= 1e-7 * M0
