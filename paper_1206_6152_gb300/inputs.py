@@ -189,7 +189,15 @@ def small_maxwell(n=(8, 6, 5), nv=(12, 10, 9), dtype="f64", seed=3,
     return Workload(**base)
 
 
+def jeans_profile() -> Workload:
+    """The 32^3-velocity Jeans set-up on a 16^3 spatial grid (537 MB of FP32 f,
+    above the 129 MB L2): the same kernels as the 32^3 x 32^3 workload at an
+    eighth of the size, for hardware-counter captures."""
+    return jeans_c2().replace(name="jeans16x32_f32", n=(16, 16, 16))
+
+
 WORKLOADS = {
+    "jeans16x32_f32": jeans_profile,
     "landau16_f64": landau_c1,
     "jeans32_f32": jeans_c2,
     "king64x32_w6": king_c3,

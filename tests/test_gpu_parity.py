@@ -144,7 +144,9 @@ def test_split_steps_match_oracle(dtype, tol, bc):
     r0 = ref.energy()
     ref.step(4)
     r1 = ref.energy()
-    assert abs(t - ref.t) <= 1e-13 * ref.t
+    # adaptive dt comes from g, i.e. from rho of the stored f: in FP32 it
+    # carries the FP32 rounding of f (relative ~1e-8)
+    assert abs(t - ref.t) <= (1e-13 if dtype == "f64" else 1e-6) * ref.t
     assert rel_l1(got, ref.f) <= tol
     assert got.min() >= 0.0
     for k, name in enumerate(["M", "K", "U", "E", "M_out"]):
