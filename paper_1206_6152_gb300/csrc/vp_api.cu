@@ -43,7 +43,7 @@ void free_ctx(vp_ctx *c)
     for (auto g : gs)
         if (g) cudaGraphExecDestroy(g);
     void *bufs[] = {c->rho, c->phi, c->g, c->cbuf, c->ghat, c->coef_kick1, c->coef_kick2,
-                    c->coef_drift, c->vc[0], c->vc[1], c->vc[2], c->red, c->rho2, c->sc,
+                    c->coef_drift, c->vc[0], c->vc[1], c->vc[2], c->red, c->rho2, c->rho_part, c->sc,
                     c->ax[0].tw, c->ax[1].tw, c->ax[2].tw, c->adj_f, c->adj_g, c->adj_lg,
                     c->adj_tmp};
     for (void *b : bufs)
@@ -157,6 +157,31 @@ int check_config(const vp_config *cfg)
     return VP_OK;
 }
 
+// host bound of |v tau / dx| over the drift tables: for the step, tau = dt,
+// which is either fixed or at most C dx_a / V^max_a on every axis
+double drift_alpha_bound(const vp_ctx *c, double tau)
+{
+    double m = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double vmax = fmax(fabs(c->cfg.vlo[a] + 0.5 * c->dv[a]),
+                                 fabs(c->cfg.vhi[a] - 0.5 * c->dv[a]));
+        double alpha;
+        if (tau > 0.0) {
+            alpha = vmax * tau / c->dx[a];
+        } else {            // adaptive dt of the step
+            const double vbox = fmax(fabs(c->cfg.vlo[a]), fabs(c->cfg.vhi[a]));
+            alpha = c->cfg.courant * vmax / vbox;
+        }
+        m = fmax(m, alpha);
+    }
+    return m;
+}
+
+double step_alpha_bound(const vp_ctx *c)
+{
+    return drift_alpha_bound(c, c->cfg.dt_fixed > 0.0 ? c->cfg.dt_fixed : -1.0);
+}
+
 int field_from_f(vp_ctx *c)
 {
     VP_CUDA_TRY(launch_density(c, c->f, c->rho));
@@ -176,12 +201,25 @@ int enqueue_prologue(vp_ctx *c)
     return VP_OK;
 }
 
+// drift z, y, x and the density of the result
+int enqueue_drift_density(vp_ctx *c)
+{
+    const double amax = step_alpha_bound(c);
+    VP_CUDA_TRY(launch_drift(c, c->f, 2, c->coef_drift, amax, nullptr));
+    VP_CUDA_TRY(launch_drift(c, c->f, 1, c->coef_drift, amax, nullptr));
+    if (c->rho_part && vp_rho_fuse_ok(c) && amax < 1.0) {
+        VP_CUDA_TRY(launch_drift(c, c->f, 0, c->coef_drift, amax, c->rho_part));
+        VP_CUDA_TRY(launch_rho_finish(c, c->rho_part, c->rho_nparts, c->rho));
+    } else {
+        VP_CUDA_TRY(launch_drift(c, c->f, 0, c->coef_drift, amax, nullptr));
+        VP_CUDA_TRY(launch_density(c, c->f, c->rho));
+    }
+    return VP_OK;
+}
+
 int enqueue_body(vp_ctx *c, int last)
 {
-    VP_CUDA_TRY(launch_drift(c, c->f, 2, c->coef_drift));
-    VP_CUDA_TRY(launch_drift(c, c->f, 1, c->coef_drift));
-    VP_CUDA_TRY(launch_drift(c, c->f, 0, c->coef_drift));
-    VP_CUDA_TRY(launch_density(c, c->f, c->rho));
+    TRY(enqueue_drift_density(c));
     VP_CUDA_TRY(launch_field_solve(c, c->rho, c->g));
     VP_CUDA_TRY(launch_coef_kick(c, c->g, &c->sc->dt, 0.5, c->coef_kick2));
     VP_CUDA_TRY(launch_advance_time(c));
@@ -357,6 +395,11 @@ int vp_init(const vp_config *cfg, void *f_dev, void *cuda_stream, vp_ctx **out)
         (r = dalloc((void **)&c->red, sizeof(double) * (2 * c->np + 64))) ||
         (r = dalloc((void **)&c->sc, sizeof(DevScalars))))
         return fail(r);
+    if (vp_rho_fuse_ok(c)) {
+        c->rho_nparts = vp_rho_parts(c);
+        if ((r = dalloc((void **)&c->rho_part, sizeof(double) * c->np * c->rho_nparts)))
+            return fail(r);
+    }
     for (int a = 0; a < 3; ++a) {
         if ((r = dalloc((void **)&c->vc[a], sizeof(double) * c->nv[a]))) return fail(r);
         std::vector<double> vc(c->nv[a]);
@@ -420,7 +463,8 @@ int vp_sweep(vp_ctx *c, int axis, double tau)
     VP_CUDA_TRY(cudaGetLastError());
     if (axis < 3) {
         VP_CUDA_TRY(launch_coef_drift(c, tau_ptr, 1.0, c->coef_drift));
-        VP_CUDA_TRY(launch_drift(c, c->f, axis, c->coef_drift));
+        VP_CUDA_TRY(launch_drift(c, c->f, axis, c->coef_drift, drift_alpha_bound(c, fabs(tau)),
+                                 nullptr));
     } else {
         VP_CUDA_TRY(launch_coef_kick(c, c->g, tau_ptr, 1.0, c->coef_kick1));
         VP_CUDA_TRY(launch_kick(c, c->f, c->coef_kick1, nullptr, 1, axis - 3));
@@ -538,15 +582,20 @@ int vp_profile_step(vp_ctx *c, double *ms_out)
     // state entering the body: K1 of this step already applied, as after
     // the prologue of vp_step; run the prologue first, untimed
     if ((r = enqueue_prologue(c)) != VP_OK) goto done;
-    PROF(rec(0));
-    PROF(launch_drift(c, c->f, 2, c->coef_drift));
-    PROF(rec(1));
-    PROF(launch_drift(c, c->f, 1, c->coef_drift));
-    PROF(rec(2));
-    PROF(launch_drift(c, c->f, 0, c->coef_drift));
-    PROF(rec(3));
-    PROF(launch_density(c, c->f, c->rho));
-    PROF(rec(4));
+    {
+        const double amax = step_alpha_bound(c);
+        const bool fuse = c->rho_part && vp_rho_fuse_ok(c) && amax < 1.0;
+        PROF(rec(0));
+        PROF(launch_drift(c, c->f, 2, c->coef_drift, amax, nullptr));
+        PROF(rec(1));
+        PROF(launch_drift(c, c->f, 1, c->coef_drift, amax, nullptr));
+        PROF(rec(2));
+        PROF(launch_drift(c, c->f, 0, c->coef_drift, amax, fuse ? c->rho_part : nullptr));
+        PROF(rec(3));
+        if (fuse) PROF(launch_rho_finish(c, c->rho_part, c->rho_nparts, c->rho));
+        else PROF(launch_density(c, c->f, c->rho));
+        PROF(rec(4));
+    }
     PROF(launch_field_solve(c, c->rho, c->g));
     PROF(rec(5));
     PROF(launch_coef_kick(c, c->g, &c->sc->dt, 0.5, c->coef_kick2));

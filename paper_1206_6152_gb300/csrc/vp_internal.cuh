@@ -77,6 +77,8 @@ struct vp_ctx {
     double *vc[3];              // velocity cell centres (device)
     double *red;                // reduction scratch (2 np + 64 doubles)
     double *rho2;               // density of the current f for diagnostics
+    double *rho_part;           // density partials of the fused x drift
+    int rho_nparts;
     DevScalars *sc;             // device scalars
     DevScalars *sc_host;        // pinned mirror for read-back
 
@@ -104,7 +106,12 @@ cudaError_t launch_coef_kick(vp_ctx *c, const double *g, const double *tau_ptr, 
                              void *out);
 cudaError_t launch_dt(vp_ctx *c, const double *g);
 cudaError_t launch_advance_time(vp_ctx *c);
-cudaError_t launch_drift(vp_ctx *c, void *f, int axis, const void *coef);
+// drift along a spatial axis; max_alpha is a host-side bound of |v tau / dx|
+// over the table (the register kernels need it below 1); with rho_part the
+// x drift also writes density partials (returns cudaErrorNotSupported if it
+// cannot)
+cudaError_t launch_drift(vp_ctx *c, void *f, int axis, const void *coef, double max_alpha,
+                         double *rho_part);
 // nsweeps velocity sweeps over every cube; sweep k runs along axis
 // (first_axis + k) % 3 with table coef_a for k < 3 and coef_b afterwards
 cudaError_t launch_kick(vp_ctx *c, void *f, const void *coef_a, const void *coef_b, int nsweeps,
@@ -117,6 +124,16 @@ cudaError_t launch_dot_rho_phi(vp_ctx *c, const double *rho, double *out2);
 cudaError_t launch_reduce_strided(vp_ctx *c, const double *in, long long n, int stride,
                                   double *out);
 int vp_sm_count();
+
+// register-line kernels (vp_sweep_fast.cu)
+int vp_kick_fast_ok(const vp_ctx *c);
+int vp_drift_fast_ok(const vp_ctx *c, int axis);
+int vp_rho_fuse_ok(const vp_ctx *c);
+int vp_rho_parts(vp_ctx *c);
+cudaError_t launch_kick_fast(vp_ctx *c, void *f, const void *ca, const void *cb, int nsweeps,
+                             int first_axis);
+cudaError_t launch_drift_fast(vp_ctx *c, void *f, int axis, const void *coef, double *rho_part);
+cudaError_t launch_rho_finish(vp_ctx *c, const double *part, int nparts, double *rho);
 
 int vp_fft_plan_axis(FFTAxis *a, int n);
 cudaError_t launch_fft(vp_ctx *c, double2 *data, int axis, int inverse);

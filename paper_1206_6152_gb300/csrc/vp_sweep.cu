@@ -468,8 +468,12 @@ cudaError_t launch_advance_time(vp_ctx *c)
     return cudaGetLastError();
 }
 
-cudaError_t launch_drift(vp_ctx *c, void *f, int axis, const void *coef)
+cudaError_t launch_drift(vp_ctx *c, void *f, int axis, const void *coef, double max_alpha,
+                         double *rho_part)
 {
+    const bool fast = vp_drift_fast_ok(c, axis) && max_alpha < 1.0;
+    if (rho_part && !(fast && axis == 0 && vp_rho_fuse_ok(c))) return cudaErrorNotSupported;
+    if (fast) return launch_drift_fast(c, f, axis, coef, rho_part);
     if (c->isdouble)
         return launch_drift_t<double>(c, (double *)f, axis, (const LineCoef<double> *)coef);
     return launch_drift_t<float>(c, (float *)f, axis, (const LineCoef<float> *)coef);
@@ -478,6 +482,7 @@ cudaError_t launch_drift(vp_ctx *c, void *f, int axis, const void *coef)
 cudaError_t launch_kick(vp_ctx *c, void *f, const void *coef_a, const void *coef_b, int nsweeps,
                         int first_axis)
 {
+    if (vp_kick_fast_ok(c)) return launch_kick_fast(c, f, coef_a, coef_b, nsweeps, first_axis);
     if (c->isdouble)
         return launch_kick_dispatch<double>(c, (double *)f, (const LineCoef<double> *)coef_a,
                                             (const LineCoef<double> *)coef_b, nsweeps,

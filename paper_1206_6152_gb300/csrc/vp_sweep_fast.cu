@@ -1,0 +1,459 @@
+// vp_sweep_fast.cu -- register-line PFC sweep kernels for the grid sizes of
+// the measured workloads (line lengths 16, 32, 48, 64), zero-shift sweeps
+// (|alpha| < 1, which every Courant-limited step satisfies).
+//
+//  * k_kick_fast<N>: one velocity cube of N^3 floats per CTA in shared memory
+//    (row pitch N + 4 floats: 16-byte aligned rows, conflict-free columns and
+//    rows).  vx and vy sweeps: each thread loads two neighbouring lines
+//    (adjacent vz) with 8-byte shared loads and updates both with packed
+//    f32x2 arithmetic; vz sweep: one contiguous line per thread with 16-byte
+//    shared loads.  A cube-sweep whose shift has a whole-cell part falls back
+//    to the generic in-place line routine.
+//  * k_drift_fast<T, N>: each thread owns two (float) or one (double)
+//    position lines, loads them straight from global memory into registers
+//    (a warp reads 256 contiguous bytes per load), updates them and stores
+//    them back.  Optionally (x sweep) it accumulates the density of the
+//    updated f: per-thread double-float sums over the velocity cells it
+//    visits, one reduction per CTA into a small partial buffer.
+#include <cuda_runtime.h>
+
+#include "vp_device.cuh"
+#include "vp_internal.cuh"
+#include "vp_line.cuh"
+
+using namespace vpline;
+
+int vp_sm_count();
+
+namespace {
+
+__device__ __forceinline__ int upos(int j, int n, int neg) { return neg ? n - 1 - j : j; }
+
+// generic in-place line update in shared memory (any whole-cell shift,
+// outflow boundaries); used only for cube-sweeps with |alpha| >= 1
+template <typename T>
+__device__ T kick_line_shifted(T *L, int st, int n, const LineCoef<T> cf)
+{
+    const int s = cf.code >> 1, neg = cf.code & 1;
+    const T c0 = cf.c0, c1 = cf.c1, c2 = cf.c2;
+    T finf = T(0);
+    for (int j = 0; j < n; ++j) finf = fmax(finf, L[j * st]);
+    T lost = T(0);
+    for (int j = (n - s > 0 ? n - s : 0); j < n; ++j) lost += L[upos(j, n, neg) * st];
+    const int jtop = n - 1 - s;
+    if (jtop < 0) {
+        for (int i = 0; i < n; ++i) L[i * st] = T(0);
+        return lost;
+    }
+    auto fget = [&](int j) -> T { return (j >= 0 && j < n) ? L[upos(j, n, neg) * st] : T(0); };
+    T f0 = fget(jtop), fm = fget(jtop - 1);
+    T ph = pfc_flux(fm, f0, fget(jtop + 1), finf, c0, c1, c2);
+    lost += ph;
+    for (int i = n - 1; i >= 0; --i) {
+        const int j = i - s;
+        if (j < 0) {
+            L[upos(i, n, neg) * st] = T(0);
+            continue;
+        }
+        const T fmm = fget(j - 2);
+        const T phm = (j >= 1) ? pfc_flux(fmm, fm, f0, finf, c0, c1, c2) : T(0);
+        L[upos(i, n, neg) * st] = (f0 - ph) + phm;
+        f0 = fm;
+        fm = fmm;
+        ph = phm;
+    }
+    return lost;
+}
+
+__device__ __forceinline__ LineW<float2> weights_pair(const LineCoef<float> &cf, float2 finf)
+{
+    LineW<float2> w;
+    const int neg = cf.code & 1;
+    weights1<float>(cf.c0, cf.c1, cf.c2, neg, finf.x, w.K0.x, w.A1.x, w.A2.x, w.ninvF.x);
+    weights1<float>(cf.c0, cf.c1, cf.c2, neg, finf.y, w.K0.y, w.A1.y, w.A2.y, w.ninvF.y);
+    return w;
+}
+
+__device__ __forceinline__ LineW<float2> weights_pair2(const LineCoef<float> &ca,
+                                                        const LineCoef<float> &cb, float2 finf)
+{
+    LineW<float2> w;
+    weights1<float>(ca.c0, ca.c1, ca.c2, ca.code & 1, finf.x, w.K0.x, w.A1.x, w.A2.x, w.ninvF.x);
+    weights1<float>(cb.c0, cb.c1, cb.c2, cb.code & 1, finf.y, w.K0.y, w.A1.y, w.A2.y, w.ninvF.y);
+    return w;
+}
+
+template <typename S>
+__device__ __forceinline__ LineW<S> weights_one(const LineCoef<S> &cf, S finf)
+{
+    LineW<S> w;
+    weights1<S>(cf.c0, cf.c1, cf.c2, cf.code & 1, finf, w.K0, w.A1, w.A2, w.ninvF);
+    return w;
+}
+
+// ---------------------------------------------------------------------------
+// kick: FP32 velocity cubes of edge N (16 or 32)
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(N * N / 2) k_kick_fast(float *__restrict__ f,
+                                                        const LineCoef<float> *__restrict__ ca,
+                                                        const LineCoef<float> *__restrict__ cb,
+                                                        int nsweeps, int first_axis, long long np,
+                                                        double *lost_out)
+{
+    constexpr int P = N + 4;              // row pitch (floats)
+    constexpr int NT = N * N / 2;         // threads
+    constexpr int NC = N * N * N;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *cube = reinterpret_cast<float *>(smem_raw);
+    __shared__ Acc<double> red[32];
+    const int t = threadIdx.x;
+    float lost = 0.f;
+    for (long long cell = blockIdx.x; cell < np; cell += gridDim.x) {
+        const float4 *g4 = reinterpret_cast<const float4 *>(f + cell * (long long)NC);
+#pragma unroll 4
+        for (int e = t; e < NC / 4; e += NT) {
+            const int r = (4 * e) / N, k = (4 * e) % N;
+            *reinterpret_cast<float4 *>(cube + r * P + k) = g4[e];
+        }
+        __syncthreads();
+        for (int sw = 0; sw < nsweeps; ++sw) {
+            const int va = (first_axis + sw) % 3;
+            const LineCoef<float> cf = (sw < 3 ? ca : cb)[cell * 3 + va];
+            if (cf.code >> 1) {
+                // whole-cell shift: generic routine on the padded cube
+                const int nl = N * N;
+                for (int l = t; l < nl; l += NT) {
+                    float *base;
+                    int st;
+                    if (va == 0) { base = cube + (l / N) * P + (l % N); st = N * P; }
+                    else if (va == 1) { base = cube + (l / N) * N * P + (l % N); st = P; }
+                    else { base = cube + l * P; st = 1; }
+                    lost += kick_line_shifted(base, st, N, cf);
+                }
+            } else if (va < 2) {
+                // two lines (vz = k, k + 1) per thread, packed
+                const int other = t / (N / 2), k = 2 * (t % (N / 2));
+                float *base = va == 0 ? cube + other * P + k : cube + other * N * P + k;
+                const int st = va == 0 ? N * P : P;
+                float2 x[N];
+#pragma unroll
+                for (int j = 0; j < N; ++j) x[j] = *reinterpret_cast<const float2 *>(base + j * st);
+                const LineW<float2> w = weights_pair(cf, line_max(x));
+                const float2 out = update_line<float2, N, false>(x, w, cf.code & 1);
+                lost += out.x + out.y;
+#pragma unroll
+                for (int j = 0; j < N; ++j) *reinterpret_cast<float2 *>(base + j * st) = x[j];
+            } else {
+                // contiguous vz lines, one per thread per pass
+#pragma unroll 1
+                for (int l = t; l < N * N; l += NT) {
+                    float *base = cube + l * P;
+                    float x[N];
+#pragma unroll
+                    for (int j = 0; j < N; j += 4) {
+                        const float4 q = *reinterpret_cast<const float4 *>(base + j);
+                        x[j] = q.x; x[j + 1] = q.y; x[j + 2] = q.z; x[j + 3] = q.w;
+                    }
+                    const LineW<float> w = weights_one<float>(cf, line_max(x));
+                    lost += update_line<float, N, false>(x, w, cf.code & 1);
+#pragma unroll
+                    for (int j = 0; j < N; j += 4)
+                        *reinterpret_cast<float4 *>(base + j) = make_float4(x[j], x[j + 1], x[j + 2], x[j + 3]);
+                }
+            }
+            __syncthreads();
+        }
+        float4 *o4 = reinterpret_cast<float4 *>(f + cell * (long long)NC);
+#pragma unroll 4
+        for (int e = t; e < NC / 4; e += NT) {
+            const int r = (4 * e) / N, k = (4 * e) % N;
+            o4[e] = *reinterpret_cast<const float4 *>(cube + r * P + k);
+        }
+        __syncthreads();
+    }
+    Acc<double> a;
+    a.add((double)lost);
+    a = block_merge(a, red);
+    if (t == 0 && a.value() != 0.0) atomicAdd(lost_out, a.value());
+}
+
+// ---------------------------------------------------------------------------
+// drift: lines along a spatial axis, held in registers
+// ---------------------------------------------------------------------------
+struct DriftGeom {
+    long long cell_stride;     // spatial-cell stride of the swept axis
+    int od;                    // outer index -> base cell: (o / od) * m1 + (o % od) * m2
+    long long m1, m2;
+    long long nvc;             // velocity cells per spatial cell
+    int va_stride, va_n;       // velocity index along the swept axis: (v / va_stride) % va_n
+    long long nunits;          // lines units (pairs for float, cells for double) per outer
+    long long per_part;        // units per CTA
+    int zremap;                // > 0: warp-uniform direction remap of the z sweep, H pairs
+    int nvz;                   // N^v_z
+    long long np;
+};
+
+template <typename T>
+struct DriftVec;
+template <>
+struct DriftVec<float> { typedef float2 V; static constexpr int W = 2; };
+template <>
+struct DriftVec<double> { typedef double V; static constexpr int W = 1; };
+
+// logical unit index -> first velocity cell of the unit
+__device__ __forceinline__ long long unit_to_v(long long L, const DriftGeom &g, int W)
+{
+    if (W == 2 && g.zremap > 0) {
+        const int H = g.zremap;           // pairs per half row
+        const int RW = 32 / H;            // rows per warp
+        const long long q = L % H;
+        long long r1 = L / H;
+        const long long ri = r1 % RW;
+        r1 /= RW;
+        const long long h = r1 & 1;
+        const long long rg = r1 >> 1;
+        const long long row = rg * RW + ri;
+        return row * g.nvz + (h * H + q) * 2;
+    }
+    return L * W;
+}
+
+template <typename T, int N, bool PERIODIC, bool RHO>
+__global__ void __launch_bounds__(128) k_drift_fast(T *__restrict__ f,
+                                                   const LineCoef<T> *__restrict__ coef,
+                                                   DriftGeom g, double *__restrict__ rho_part,
+                                                   double *lost_out)
+{
+    typedef typename DriftVec<T>::V V;
+    constexpr int W = DriftVec<T>::W;
+    __shared__ Acc<double> red[32];
+    const int o = blockIdx.y;
+    const long long base_cell = (long long)(o / g.od) * g.m1 + (long long)(o % g.od) * g.m2;
+    const long long gstride = g.cell_stride * g.nvc;
+    T *fb = f + base_cell * g.nvc;
+    const long long u0 = (long long)blockIdx.x * g.per_part;
+    long long u1 = u0 + g.per_part;
+    if (u1 > g.nunits) u1 = g.nunits;
+    Acc<T> acc[RHO ? N : 1];
+    T lost = T(0);
+    for (long long L = u0 + threadIdx.x; L < u1; L += blockDim.x) {
+        const long long v = unit_to_v(L, g, W);
+        V x[N];
+        T *p = fb + v;
+#pragma unroll
+        for (int j = 0; j < N; ++j) x[j] = *reinterpret_cast<const V *>(p + j * gstride);
+        if constexpr (W == 2) {
+            const int via = (int)((v / g.va_stride) % g.va_n);
+            const int vib = (int)(((v + 1) / g.va_stride) % g.va_n);
+            const LineCoef<float> ca = coef[via];
+            const LineCoef<float> cb = coef[vib];
+            if ((ca.code & 1) == (cb.code & 1)) {
+                const LineW<float2> w = weights_pair2(ca, cb, line_max(x));
+                const float2 out = update_line<float2, N, PERIODIC>(x, w, ca.code & 1);
+                lost += out.x + out.y;
+            } else {
+                // the pair straddles the sign change of the velocity: two
+                // scalar lines
+                float y0[N], y1[N];
+#pragma unroll
+                for (int j = 0; j < N; ++j) { y0[j] = x[j].x; y1[j] = x[j].y; }
+                const LineW<float> w0 = weights_one<float>(ca, line_max(y0));
+                const LineW<float> w1 = weights_one<float>(cb, line_max(y1));
+                lost += update_line<float, N, PERIODIC>(y0, w0, ca.code & 1);
+                lost += update_line<float, N, PERIODIC>(y1, w1, cb.code & 1);
+#pragma unroll
+                for (int j = 0; j < N; ++j) x[j] = make_float2(y0[j], y1[j]);
+            }
+        } else {
+            const int via = (int)((v / g.va_stride) % g.va_n);
+            const LineCoef<T> ca = coef[via];
+            const LineW<V> w = weights_one<T>(ca, line_max(x));
+            lost += update_line<V, N, PERIODIC>(x, w, ca.code & 1);
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) *reinterpret_cast<V *>(p + j * gstride) = x[j];
+        if constexpr (RHO) {
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                if constexpr (W == 2) { acc[j].add(x[j].x); acc[j].add(x[j].y); }
+                else acc[j].add(x[j]);
+            }
+        }
+    }
+    if constexpr (RHO) {
+        // per-x reduction over the CTA, written as one partial per (part, cell)
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            Acc<T> a = block_merge(acc[j], reinterpret_cast<Acc<T> *>(red));
+            if (threadIdx.x == 0)
+                rho_part[(long long)blockIdx.x * g.np + base_cell + j * g.cell_stride] = a.value();
+            __syncthreads();
+        }
+    }
+    if (!PERIODIC) {
+        Acc<double> a;
+        a.add((double)lost);
+        a = block_merge(a, red);
+        if (threadIdx.x == 0 && a.value() != 0.0) atomicAdd(lost_out, a.value());
+    }
+}
+
+// rho = dvol * sum_parts partial (Neumaier)
+__global__ void k_rho_finish(const double *__restrict__ part, int nparts, long long np, double dvol,
+                             double *__restrict__ rho)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= np) return;
+    Acc<double> a;
+    for (int p = 0; p < nparts; ++p) a.add(part[(long long)p * np + t]);
+    rho[t] = a.value() * dvol;
+}
+
+template <int N>
+cudaError_t kick_fast_n(vp_ctx *c, float *f, const LineCoef<float> *ca, const LineCoef<float> *cb,
+                        int nsweeps, int first_axis)
+{
+    constexpr int P = N + 4;
+    const size_t smem = (size_t)N * N * P * sizeof(float);
+    auto kern = k_kick_fast<N>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, N * N / 2, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    long long grid = (long long)per_sm * vp_sm_count();
+    if (grid > c->np) grid = c->np;
+    kern<<<(unsigned)grid, N * N / 2, smem, c->stream>>>(f, ca, cb, nsweeps, first_axis, c->np,
+                                                          &c->sc->lost);
+    return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t drift_fast_n(vp_ctx *c, T *f, int axis, const LineCoef<T> *coef, double *rho_part,
+                         int nparts)
+{
+    DriftGeom g;
+    if (axis == 0) {
+        g.cell_stride = (long long)c->n[1] * c->n[2];
+        g.od = 1; g.m1 = 1; g.m2 = 0;
+    } else if (axis == 1) {
+        g.cell_stride = c->n[2];
+        g.od = c->n[2]; g.m1 = (long long)c->n[1] * c->n[2]; g.m2 = 1;
+    } else {
+        g.cell_stride = 1;
+        g.od = 1; g.m1 = c->n[2]; g.m2 = 0;
+    }
+    constexpr int W = DriftVec<T>::W;
+    g.nvc = c->nvc;
+    g.va_stride = axis == 0 ? c->nv[1] * c->nv[2] : (axis == 1 ? c->nv[2] : 1);
+    g.va_n = c->nv[axis];
+    g.nunits = c->nvc / W;
+    g.nvz = c->nv[2];
+    g.np = c->np;
+    g.zremap = 0;
+    if (W == 2 && axis == 2 && c->nv[2] % 4 == 0) {
+        const int H = c->nv[2] / 4;
+        if (32 % H == 0 && ((long long)c->nv[0] * c->nv[1]) % (2 * (32 / H)) == 0) g.zremap = H;
+    }
+    const long long outer = c->np / N;
+    if (nparts <= 0) {
+        long long target = 4LL * 4 * vp_sm_count();
+        nparts = (int)((target + outer - 1) / outer);
+        if (nparts < 1) nparts = 1;
+        const long long maxparts = (g.nunits + 127) / 128;
+        if (nparts > maxparts) nparts = (int)maxparts;
+    }
+    g.per_part = (g.nunits + nparts - 1) / nparts;
+    dim3 grid((unsigned)nparts, (unsigned)outer);
+    const bool rho = rho_part != nullptr;
+    constexpr bool RHO_OK = (sizeof(T) == 4 && N <= 32) || N <= 16;
+    if (rho && !RHO_OK) return cudaErrorNotSupported;
+    if (c->periodic_space) {
+        if constexpr (RHO_OK)
+            if (rho) {
+                k_drift_fast<T, N, true, true><<<grid, 128, 0, c->stream>>>(f, coef, g, rho_part, &c->sc->lost);
+                return cudaGetLastError();
+            }
+        k_drift_fast<T, N, true, false><<<grid, 128, 0, c->stream>>>(f, coef, g, rho_part, &c->sc->lost);
+    } else {
+        if constexpr (RHO_OK)
+            if (rho) {
+                k_drift_fast<T, N, false, true><<<grid, 128, 0, c->stream>>>(f, coef, g, rho_part, &c->sc->lost);
+                return cudaGetLastError();
+            }
+        k_drift_fast<T, N, false, false><<<grid, 128, 0, c->stream>>>(f, coef, g, rho_part, &c->sc->lost);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// number of density partials the fused x drift writes per spatial cell
+int vp_rho_parts(vp_ctx *c)
+{
+    const long long outer = c->np / c->n[0];
+    long long target = 4LL * 4 * vp_sm_count();
+    int nparts = (int)((target + outer - 1) / outer);
+    if (nparts < 1) nparts = 1;
+    const long long nunits = c->nvc / (c->isdouble ? 1 : 2);
+    const long long maxparts = (nunits + 127) / 128;
+    if (nparts > maxparts) nparts = (int)maxparts;
+    return nparts;
+}
+
+// 1 if the register kernels handle this grid
+int vp_kick_fast_ok(const vp_ctx *c)
+{
+    const int n = c->nv[0];
+    return !c->isdouble && n == c->nv[1] && n == c->nv[2] && (n == 16 || n == 32);
+}
+
+int vp_drift_fast_ok(const vp_ctx *c, int axis)
+{
+    const int n = c->n[axis];
+    if (!(n == 16 || n == 32 || n == 48 || n == 64)) return 0;
+    if (!c->isdouble && (c->nvc % 2 != 0)) return 0;
+    if (c->isdouble && n > 16) return 0;
+    return 1;
+}
+
+int vp_rho_fuse_ok(const vp_ctx *c)
+{
+    return vp_drift_fast_ok(c, 0) && c->n[0] <= (c->isdouble ? 16 : 32);
+}
+
+cudaError_t launch_kick_fast(vp_ctx *c, void *f, const void *ca, const void *cb, int nsweeps,
+                             int first_axis)
+{
+    if (c->nv[0] == 32)
+        return kick_fast_n<32>(c, (float *)f, (const LineCoef<float> *)ca,
+                               (const LineCoef<float> *)cb, nsweeps, first_axis);
+    return kick_fast_n<16>(c, (float *)f, (const LineCoef<float> *)ca, (const LineCoef<float> *)cb,
+                           nsweeps, first_axis);
+}
+
+cudaError_t launch_drift_fast(vp_ctx *c, void *f, int axis, const void *coef, double *rho_part)
+{
+    const int n = c->n[axis];
+    const int np = rho_part ? vp_rho_parts(c) : 0;
+    if (c->isdouble) {
+        const LineCoef<double> *cf = (const LineCoef<double> *)coef + (size_t)axis * c->maxnv;
+        return drift_fast_n<double, 16>(c, (double *)f, axis, cf, rho_part, np);
+    }
+    const LineCoef<float> *cf = (const LineCoef<float> *)coef + (size_t)axis * c->maxnv;
+    switch (n) {
+    case 16: return drift_fast_n<float, 16>(c, (float *)f, axis, cf, rho_part, np);
+    case 32: return drift_fast_n<float, 32>(c, (float *)f, axis, cf, rho_part, np);
+    case 48: return drift_fast_n<float, 48>(c, (float *)f, axis, cf, nullptr, 0);
+    default: return drift_fast_n<float, 64>(c, (float *)f, axis, cf, nullptr, 0);
+    }
+}
+
+cudaError_t launch_rho_finish(vp_ctx *c, const double *part, int nparts, double *rho)
+{
+    k_rho_finish<<<(unsigned)((c->np + 255) / 256), 256, 0, c->stream>>>(part, nparts, c->np,
+                                                                        c->dvol_v, rho);
+    return cudaGetLastError();
+}

@@ -45,6 +45,10 @@ SMALL = [
     dict(n=(8, 6, 5), nv=(12, 10, 9)),
     dict(n=(7, 1, 3), nv=(5, 8, 1)),
     dict(n=(4, 4, 4), nv=(16, 16, 16)),
+    # sizes served by the register-line kernels (line lengths 16/32, even
+    # velocity counts, a 32-cell vz axis for the warp-uniform z mapping)
+    dict(n=(16, 32, 16), nv=(4, 6, 10)),
+    dict(n=(16, 16, 16), nv=(2, 4, 32)),
 ]
 
 
@@ -154,6 +158,29 @@ def test_split_steps_match_oracle(dtype, tol, bc):
         assert abs(e1[name] - r1[k]) <= 10 * tol * scale, name
         if name != "M_out":
             assert abs(e0[name] - r0[k]) <= 1e-12 * scale, name
+    sim.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-11), ("f32", 1e-5)])
+def test_split_steps_register_kernels(dtype, tol):
+    """16^3 x 16^3 with a density-sensitive field: the register kick (FP32),
+    the register drifts with the fused density (both dtypes)."""
+    w = I.small_maxwell(n=(16, 16, 16), nv=(16, 16, 16), dtype=dtype, amp=0.3, G=25.0)
+    w = w.replace(box_lo=(-0.5,) * 3, box_hi=(0.5,) * 3, vlo=(-4.0,) * 3, vhi=(4.0,) * 3)
+    f0 = I.initial_condition(w)
+    sim, f = gpu_sim(w, f0)
+    t = sim.step(4, sync=True)
+    got = f.cpu().numpy().astype(np.float64)
+    rho_g = sim.field()[0].cpu().numpy()
+    ref = O.Simulation(f0, O.Grid.of(w), O.Params.of(w))
+    ref.step(4)
+    assert abs(t - ref.t) <= (1e-13 if dtype == "f64" else 1e-6) * ref.t
+    assert rel_l1(got, ref.f) <= tol
+    assert got.min() >= 0.0
+    # the fused density of the last drift matches the oracle's field solve input
+    f_b = ref.rho
+    assert np.abs(rho_g - f_b).max() <= (1e-12 if dtype == "f64" else 2e-6) * f_b.max()
     sim.close()
 
 
