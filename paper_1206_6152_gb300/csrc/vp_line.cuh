@@ -109,13 +109,12 @@ struct LineW {
 
 // component-wise line maximum
 template <int N>
+__device__ __forceinline__ float tree_max(const float (&v)[N]);
+
+template <int N>
 __device__ __forceinline__ float line_max(const float (&x)[N])
 {
-    float m = 0.f;
-#pragma unroll
-    for (int j = 0; j + 1 < N; j += 2) m = max3(m, x[j], x[j + 1]);
-    if (N & 1) m = fmaxf(m, x[N - 1]);
-    return m;
+    return fmaxf(tree_max<N>(x), 0.f);
 }
 template <int N>
 __device__ __forceinline__ double line_max(const double (&x)[N])
@@ -125,21 +124,39 @@ __device__ __forceinline__ double line_max(const double (&x)[N])
     for (int j = 0; j < N; ++j) m = fmax(m, x[j]);
     return m;
 }
+// tree of 3-input maxima (short dependency chain)
+template <int N>
+__device__ __forceinline__ float tree_max(const float (&v)[N])
+{
+    if constexpr (N == 1) {
+        return v[0];
+    } else if constexpr (N == 2) {
+        return fmaxf(v[0], v[1]);
+    } else {
+        constexpr int M = (N + 2) / 3;
+        float w[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const int a = 3 * i;
+            if (a + 2 < N) w[i] = max3(v[a], v[a + 1], v[a + 2]);
+            else if (a + 1 < N) w[i] = fmaxf(v[a], v[a + 1]);
+            else w[i] = v[a];
+        }
+        return tree_max<M>(w);
+    }
+}
+
 template <int N>
 __device__ __forceinline__ float2 line_max(const float2 (&x)[N])
 {
-    float mx = 0.f, my = 0.f;
+    float vx[N], vy[N];
 #pragma unroll
-    for (int j = 0; j + 1 < N; j += 2) {
-        mx = max3(mx, x[j].x, x[j + 1].x);
-        my = max3(my, x[j].y, x[j + 1].y);
-    }
-    if (N & 1) {
-        mx = fmaxf(mx, x[N - 1].x);
-        my = fmaxf(my, x[N - 1].y);
-    }
-    return make_float2(mx, my);
+    for (int j = 0; j < N; ++j) { vx[j] = x[j].x; vy[j] = x[j].y; }
+    return make_float2(fmaxf(tree_max<N>(vx), 0.f), fmaxf(tree_max<N>(vy), 0.f));
 }
+
+__device__ __forceinline__ float recip(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ double recip(double a) { return __drcp_rn(a); }
 
 // weights from (c0, c1, c2), direction and the line maximum, one component
 template <typename S>
@@ -150,7 +167,7 @@ __device__ __forceinline__ void weights1(S c0, S c1, S c2, int neg, S finf, S &K
     K0 = c0 + S(2) * (c1 - c2);
     A1 = neg ? c2 * F : -c1 * F;
     A2 = neg ? -c1 * F : c2 * F;
-    ninvF = F > S(0) ? S(-1) / F : S(0);
+    ninvF = F > S(0) ? -recip(F) : S(0);
 }
 
 // phi of one cell from its left, own and right values

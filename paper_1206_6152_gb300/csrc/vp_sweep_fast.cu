@@ -32,7 +32,7 @@ __device__ __forceinline__ int upos(int j, int n, int neg) { return neg ? n - 1 
 // generic in-place line update in shared memory (any whole-cell shift,
 // outflow boundaries); used only for cube-sweeps with |alpha| >= 1
 template <typename T>
-__device__ T kick_line_shifted(T *L, int st, int n, const LineCoef<T> cf)
+__device__ __noinline__ T kick_line_shifted(T *L, int st, int n, const LineCoef<T> cf)
 {
     const int s = cf.code >> 1, neg = cf.code & 1;
     const T c0 = cf.c0, c1 = cf.c1, c2 = cf.c2;
@@ -93,84 +93,204 @@ __device__ __forceinline__ LineW<S> weights_one(const LineCoef<S> &cf, S finf)
 
 // ---------------------------------------------------------------------------
 // kick: FP32 velocity cubes of edge N (16 or 32)
+//
+// Line ownership: for sweeps along vx and vy each thread owns the two lines
+// at vz = k, k + 1 of one (vy resp. vx) index; for vz it owns two contiguous
+// rows.  The first sweep of a cube reads its lines straight from global
+// memory into registers and the last one writes them straight back, so the
+// cube crosses shared memory only between sweeps.  The next cube's loads are
+// issued before the barrier that protects the buffer, so they overlap the
+// end of the previous cube.
 // ---------------------------------------------------------------------------
 template <int N>
-__global__ void __launch_bounds__(N * N / 2) k_kick_fast(float *__restrict__ f,
-                                                        const LineCoef<float> *__restrict__ ca,
-                                                        const LineCoef<float> *__restrict__ cb,
-                                                        int nsweeps, int first_axis, long long np,
-                                                        double *lost_out)
+struct KickCube {
+    static constexpr int P = N + 4;           // row pitch (floats)
+    static constexpr int NU = N * N / 2;      // units of two packed lines per sweep
+    static constexpr int NT = NU;             // threads: one unit each
+    static constexpr int NC = N * N * N;
+};
+
+// element (i, j, k) of the cube: global offset and shared offset
+template <int N>
+__device__ __forceinline__ int goff(int i, int j, int k) { return (i * N + j) * N + k; }
+template <int N>
+__device__ __forceinline__ int soff(int i, int j, int k) { return (i * N + j) * KickCube<N>::P + k; }
+
+// pair lines along va (0: vx, 1: vy) owned by thread t: returns the element
+// offsets of line cell j through base + j * step (k is even)
+template <int N, bool GLOBAL>
+__device__ __forceinline__ void pair_geom(int va, int t, int &base, int &step)
 {
-    constexpr int P = N + 4;              // row pitch (floats)
-    constexpr int NT = N * N / 2;         // threads
-    constexpr int NC = N * N * N;
+    const int other = t / (N / 2), k = 2 * (t % (N / 2));
+    if (va == 0) {
+        base = GLOBAL ? goff<N>(0, other, k) : soff<N>(0, other, k);
+        step = GLOBAL ? N * N : N * KickCube<N>::P;
+    } else {
+        base = GLOBAL ? goff<N>(other, 0, k) : soff<N>(other, 0, k);
+        step = GLOBAL ? N : KickCube<N>::P;
+    }
+}
+
+template <int N, bool GLOBAL>
+__device__ __forceinline__ void load_pairs(const float *src, int va, int t, float2 (&x)[N])
+{
+    int base, step;
+    pair_geom<N, GLOBAL>(va, t, base, step);
+#pragma unroll
+    for (int j = 0; j < N; ++j) x[j] = *reinterpret_cast<const float2 *>(src + base + j * step);
+}
+
+template <int N, bool GLOBAL>
+__device__ __forceinline__ void store_pairs(float *dst, int va, int t, const float2 (&x)[N])
+{
+    int base, step;
+    pair_geom<N, GLOBAL>(va, t, base, step);
+#pragma unroll
+    for (int j = 0; j < N; ++j) *reinterpret_cast<float2 *>(dst + base + j * step) = x[j];
+}
+
+// rows (vz lines) (i, j) = (2q, j) and (2q + 1, j) with q = t / N, j = t % N,
+// packed as one float2 line x[k] = (row a cell k, row b cell k).  A warp
+// owns the same vx planes here as in the vy sweep (plane t / (N/2)), so a
+// vy -> vz (or vz -> vy) transition only needs a warp barrier.
+template <int N>
+__device__ __forceinline__ void row_pair(int t, int &ra, int &rb)
+{
+    const int q = t / N, j = t % N;
+    ra = (2 * q) * N + j;
+    rb = (2 * q + 1) * N + j;
+}
+
+template <int N, bool GLOBAL>
+__device__ __forceinline__ void load_rows(const float *src, int t, float2 (&x)[N])
+{
+    int r0, r1;
+    row_pair<N>(t, r0, r1);
+    const float *ra = src + (GLOBAL ? r0 * N : r0 * KickCube<N>::P);
+    const float *rb = src + (GLOBAL ? r1 * N : r1 * KickCube<N>::P);
+#pragma unroll
+    for (int j = 0; j < N; j += 4) {
+        const float4 qa = *reinterpret_cast<const float4 *>(ra + j);
+        const float4 qb = *reinterpret_cast<const float4 *>(rb + j);
+        x[j] = make_float2(qa.x, qb.x);
+        x[j + 1] = make_float2(qa.y, qb.y);
+        x[j + 2] = make_float2(qa.z, qb.z);
+        x[j + 3] = make_float2(qa.w, qb.w);
+    }
+}
+
+template <int N, bool GLOBAL>
+__device__ __forceinline__ void store_rows(float *dst, int t, const float2 (&x)[N])
+{
+    int r0, r1;
+    row_pair<N>(t, r0, r1);
+    float *ra = dst + (GLOBAL ? r0 * N : r0 * KickCube<N>::P);
+    float *rb = dst + (GLOBAL ? r1 * N : r1 * KickCube<N>::P);
+#pragma unroll
+    for (int j = 0; j < N; j += 4) {
+        *reinterpret_cast<float4 *>(ra + j) = make_float4(x[j].x, x[j + 1].x, x[j + 2].x, x[j + 3].x);
+        *reinterpret_cast<float4 *>(rb + j) = make_float4(x[j].y, x[j + 1].y, x[j + 2].y, x[j + 3].y);
+    }
+}
+
+// one sweep of the owned lines held in registers
+template <int N>
+__device__ __forceinline__ float sweep_pairs(float2 (&x)[N], const LineCoef<float> &cf)
+{
+    const LineW<float2> w = weights_pair(cf, line_max(x));
+    const float2 out = update_line<float2, N, false>(x, w, cf.code & 1);
+    return out.x + out.y;
+}
+
+
+// whole cube through shared memory (a sweep moves by whole cells)
+template <int N>
+__device__ __noinline__ float kick_cube_shifted(float *g, float *cube, const LineCoef<float> *cf,
+                                                int nsweeps, int first_axis)
+{
+    constexpr int P = KickCube<N>::P;
+    constexpr int NT = KickCube<N>::NT;
+    constexpr int NC = KickCube<N>::NC;
+    const int t = threadIdx.x;
+    float lost = 0.f;
+    for (int e = t; e < NC / 4; e += NT) {
+        const int r = (4 * e) / N, k = (4 * e) % N;
+        *reinterpret_cast<float4 *>(cube + r * P + k) = reinterpret_cast<const float4 *>(g)[e];
+    }
+    __syncthreads();
+    for (int sw = 0; sw < nsweeps; ++sw) {
+        const int va = (first_axis + sw) % 3;
+        const LineCoef<float> c = cf[sw];
+        for (int l = t; l < N * N; l += NT) {
+            float *base;
+            int st;
+            if (va == 0) { base = cube + (l / N) * P + (l % N); st = N * P; }
+            else if (va == 1) { base = cube + (l / N) * N * P + (l % N); st = P; }
+            else { base = cube + l * P; st = 1; }
+            lost += kick_line_shifted(base, st, N, c);
+        }
+        __syncthreads();
+    }
+    for (int e = t; e < NC / 4; e += NT) {
+        const int r = (4 * e) / N, k = (4 * e) % N;
+        reinterpret_cast<float4 *>(g)[e] = *reinterpret_cast<const float4 *>(cube + r * P + k);
+    }
+    return lost;
+}
+
+template <int N>
+__global__ void __launch_bounds__(KickCube<N>::NT) k_kick_fast(float *__restrict__ f,
+                                                             const LineCoef<float> *__restrict__ ca,
+                                                             const LineCoef<float> *__restrict__ cb,
+                                                             int nsweeps, int first_axis, long long np,
+                                                             double *lost_out)
+{
+    constexpr int NC = KickCube<N>::NC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *cube = reinterpret_cast<float *>(smem_raw);
     __shared__ Acc<double> red[32];
+    __shared__ LineCoef<float> scf[2][6];
     const int t = threadIdx.x;
     float lost = 0.f;
-    for (long long cell = blockIdx.x; cell < np; cell += gridDim.x) {
-        const float4 *g4 = reinterpret_cast<const float4 *>(f + cell * (long long)NC);
-#pragma unroll 4
-        for (int e = t; e < NC / 4; e += NT) {
-            const int r = (4 * e) / N, k = (4 * e) % N;
-            *reinterpret_cast<float4 *>(cube + r * P + k) = g4[e];
-        }
+    int par = 0;
+    for (long long cell = blockIdx.x; cell < np; cell += gridDim.x, par ^= 1) {
+        float *g = f + cell * (long long)NC;
+        if (t < nsweeps) scf[par][t] = (t < 3 ? ca : cb)[cell * 3 + (first_axis + t) % 3];
+        // first sweep: lines straight from global memory, issued before the
+        // barrier that publishes the coefficients and retires the previous
+        // cube's readers of the buffer
+        float2 x[N];
+        if (first_axis < 2) load_pairs<N, true>(g, first_axis, t, x);
+        else load_rows<N, true>(g, t, x);
         __syncthreads();
+        bool shifted = false;
+        for (int sw = 0; sw < nsweeps; ++sw) shifted |= (scf[par][sw].code >> 1) != 0;
+        if (shifted) {
+            lost += kick_cube_shifted<N>(g, cube, scf[par], nsweeps, first_axis);
+            continue;
+        }
         for (int sw = 0; sw < nsweeps; ++sw) {
             const int va = (first_axis + sw) % 3;
-            const LineCoef<float> cf = (sw < 3 ? ca : cb)[cell * 3 + va];
-            if (cf.code >> 1) {
-                // whole-cell shift: generic routine on the padded cube
-                const int nl = N * N;
-                for (int l = t; l < nl; l += NT) {
-                    float *base;
-                    int st;
-                    if (va == 0) { base = cube + (l / N) * P + (l % N); st = N * P; }
-                    else if (va == 1) { base = cube + (l / N) * N * P + (l % N); st = P; }
-                    else { base = cube + l * P; st = 1; }
-                    lost += kick_line_shifted(base, st, N, cf);
-                }
-            } else if (va < 2) {
-                // two lines (vz = k, k + 1) per thread, packed
-                const int other = t / (N / 2), k = 2 * (t % (N / 2));
-                float *base = va == 0 ? cube + other * P + k : cube + other * N * P + k;
-                const int st = va == 0 ? N * P : P;
-                float2 x[N];
-#pragma unroll
-                for (int j = 0; j < N; ++j) x[j] = *reinterpret_cast<const float2 *>(base + j * st);
-                const LineW<float2> w = weights_pair(cf, line_max(x));
-                const float2 out = update_line<float2, N, false>(x, w, cf.code & 1);
-                lost += out.x + out.y;
-#pragma unroll
-                for (int j = 0; j < N; ++j) *reinterpret_cast<float2 *>(base + j * st) = x[j];
-            } else {
-                // contiguous vz lines, one per thread per pass
-#pragma unroll 1
-                for (int l = t; l < N * N; l += NT) {
-                    float *base = cube + l * P;
-                    float x[N];
-#pragma unroll
-                    for (int j = 0; j < N; j += 4) {
-                        const float4 q = *reinterpret_cast<const float4 *>(base + j);
-                        x[j] = q.x; x[j + 1] = q.y; x[j + 2] = q.z; x[j + 3] = q.w;
-                    }
-                    const LineW<float> w = weights_one<float>(cf, line_max(x));
-                    lost += update_line<float, N, false>(x, w, cf.code & 1);
-#pragma unroll
-                    for (int j = 0; j < N; j += 4)
-                        *reinterpret_cast<float4 *>(base + j) = make_float4(x[j], x[j + 1], x[j + 2], x[j + 3]);
-                }
+            const bool last = sw == nsweeps - 1;
+            const LineCoef<float> cf = scf[par][sw];
+            if (sw) {
+                if (va < 2) load_pairs<N, false>(cube, va, t, x);
+                else load_rows<N, false>(cube, t, x);
             }
-            __syncthreads();
+            lost += sweep_pairs<N>(x, cf);
+            if (va < 2) {
+                if (last) store_pairs<N, true>(g, va, t, x);
+                else store_pairs<N, false>(cube, va, t, x);
+            } else {
+                if (last) store_rows<N, true>(g, t, x);
+                else store_rows<N, false>(cube, t, x);
+            }
+            if (!last) {
+                const int vb = (first_axis + sw + 1) % 3;
+                if (va + vb == 3) __syncwarp();     // vy <-> vz: planes stay with the warp
+                else __syncthreads();
+            }
         }
-        float4 *o4 = reinterpret_cast<float4 *>(f + cell * (long long)NC);
-#pragma unroll 4
-        for (int e = t; e < NC / 4; e += NT) {
-            const int r = (4 * e) / N, k = (4 * e) % N;
-            o4[e] = *reinterpret_cast<const float4 *>(cube + r * P + k);
-        }
-        __syncthreads();
     }
     Acc<double> a;
     a.add((double)lost);
@@ -314,19 +434,20 @@ template <int N>
 cudaError_t kick_fast_n(vp_ctx *c, float *f, const LineCoef<float> *ca, const LineCoef<float> *cb,
                         int nsweeps, int first_axis)
 {
-    constexpr int P = N + 4;
+    constexpr int P = KickCube<N>::P;
     const size_t smem = (size_t)N * N * P * sizeof(float);
     auto kern = k_kick_fast<N>;
+    const int threads = KickCube<N>::NT;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, N * N / 2, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     long long grid = (long long)per_sm * vp_sm_count();
     if (grid > c->np) grid = c->np;
-    kern<<<(unsigned)grid, N * N / 2, smem, c->stream>>>(f, ca, cb, nsweeps, first_axis, c->np,
-                                                          &c->sc->lost);
+    kern<<<(unsigned)grid, threads, smem, c->stream>>>(f, ca, cb, nsweeps, first_axis, c->np,
+                                                       &c->sc->lost);
     return cudaGetLastError();
 }
 

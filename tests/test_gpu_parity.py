@@ -78,7 +78,8 @@ def test_each_sweep_matches_oracle(shape, dtype, space_bc):
                 O.sweep(ref, axis, grid.vc(axis), tau, grid.dx[axis], per)
             else:
                 O.sweep(ref, axis, acc[axis - 3], tau, grid.dv[axis - 3], False)
-            err = np.abs(got - ref).max() / ref.max()
+            # (a large outflow shift can empty the grid: scale by the input)
+            err = np.abs(got - ref).max() / float(f0.max())
             assert err <= tol_max, (axis, tau, err)
             assert got.min() >= 0.0
     sim.close()
