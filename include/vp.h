@@ -152,7 +152,9 @@ int vp_stats(vp_ctx *ctx, long long *kernels_launched);
 
 /* Discrete adjoint of one split step (not in the paper; limiter branches,
  * integer shifts and line-maximum positions frozen at the forward pass).
- * Requires dt_fixed > 0.
+ * Requires dt_fixed > 0 (VP_ERR_STATE otherwise).  On first use the
+ * context allocates nine scratch states (the inputs of the nine sweeps of
+ * the replayed step) plus small tables; VP_ERR_OOM if they do not fit.
  *   f_start: the step-start f^n (device, same layout/dtype as f; read only)
  *   g_start: the step-start acceleration g^n (3 N^p doubles, device)
  *   lambda_f: in: cotangent of f^{n+1}; out: cotangent of f^n (device,
@@ -162,19 +164,28 @@ int vp_stats(vp_ctx *ctx, long long *kernels_launched);
  * The context's own f is not modified; the context's scratch is used to
  * replay the forward step. */
 int vp_adjoint_step(vp_ctx *ctx, const void *f_start, const double *g_start,
-                    double *lambda_f, double *lambda_g);
+                    void *lambda_f, double *lambda_g);
+
+/* Adjoint of one sweep T_axis(tau) (as vp_sweep) at the input f_in (device,
+ * f layout and dtype): lambda (device, same layout and dtype) holds the
+ * cotangent of the sweep output on entry and that of the input on exit.
+ * For velocity axes the cotangent of the acceleration component is added
+ * to lambda_g (3 N^p doubles, device; may be NULL).  The kick shifts use the
+ * context's current g. */
+int vp_sweep_adjoint(vp_ctx *ctx, int axis, double tau, const void *f_in, void *lambda,
+                     double *lambda_g);
 
 /* Adds to lambda_f (device, f layout and dtype) the cotangent of f that
  * flows back through g = -grad phi[rho(f)] from lambda_g (3 N^p doubles,
  * device).  Used for g^0 = field(f^0) at the start of a trajectory. */
-int vp_field_adjoint(vp_ctx *ctx, const double *lambda_g, double *lambda_f);
+int vp_field_adjoint(vp_ctx *ctx, const double *lambda_g, void *lambda_f);
 
 /* Cotangent of f for a final-time functional of the current f:
  * kind 0: J = U = 1/2 sum rho phi dV_x; kind 1: J = 1/2 sum (rho -
  * target)^2 dV_x with target (N^p doubles, device).  Writes dJ/df into
  * lambda_f (device, f layout and dtype) and J into *J_out (host; this
  * synchronises). */
-int vp_functional(vp_ctx *ctx, int kind, const double *target, double *lambda_f,
+int vp_functional(vp_ctx *ctx, int kind, const double *target, void *lambda_f,
                   double *J_out);
 
 /* Releases everything the context owns (not f). */

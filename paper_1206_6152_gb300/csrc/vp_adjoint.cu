@@ -1,28 +1,516 @@
 // vp_adjoint.cu -- discrete adjoint of the split step (not in the paper).
+//
+// The forward sweep of one line is, in its upwind frame with shift
+// |alpha| = s + beta,
+//   out_i = f_{i-s} - phi_{i-s} + phi_{i-s-1},
+//   phi_j = c0 f_j + c1 E+_j + c2 E-_j,
+//   E+_j  = clamp(f_{j+1} - f_j, -2 (finf - f_j), 2 f_j),
+//   E-_j  = clamp(f_j - f_{j-1}, -2 f_j, 2 (finf - f_j)),
+// c0 = beta, c1 = beta (1-beta)(2-beta)/6, c2 = beta (1-beta)(1+beta)/6 and
+// finf the line maximum.  With every clamp arm, the integer shift s and the
+// position of the line maximum frozen at the forward input, the map is
+// linear in f; its transpose is applied here line by line.  The shift's
+// fractional part also depends on the acceleration in velocity sweeps:
+//   d out_i / d beta = -phi'_{i-s} + phi'_{i-s-1},
+//   phi'_j = f_j + c1'(beta) E+_j + c2'(beta) E-_j,
+// which gives the cotangent of g through alpha = g tau / dv.  Arms: an E arm
+// is limited only when the difference lies strictly beyond its bound; the
+// cotangent of finf goes to the first maximum in upwind order.  The
+// rounding guard phi <= f of the forward kernels is treated as inactive.
+//
+// The field part reverses g = -grad phi, phi = G * rho, rho = dv^3 sum_v f:
+// the transposed central difference, the same (symmetric) convolution, and
+// a broadcast over velocity.
 #include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <vector>
 
 #include "vp_device.cuh"
 #include "vp_internal.cuh"
 
+int vp_sm_count();
+
+namespace {
+
+struct LineGeom {
+    int axis;                 // 0..5
+    int n;                    // line length
+    // position axes: line (o, v): base = cell(o) * nvc + v
+    long long cell_stride;
+    int od;
+    long long m1, m2;
+    // velocity axes: line (cell, w): base = cell * nvc + voff(w), stride vstride
+    int wdiv, wmul_hi, wmul_lo;   // voff = (w / wdiv) * wmul_hi + (w % wdiv) * wmul_lo
+    long long nvc;
+    long long stride;             // element stride along the line
+    long long nlines_inner;       // v cells (position axes) or lines per cube (velocity)
+};
+
+template <typename T>
+struct AdjArgs {
+    const T *fin;                 // sweep input
+    T *lam;                       // in: cotangent of the output, out: of the input
+    const LineCoef<T> *coef;      // position axes: [maxnv] of this axis; velocity: [np][3]
+    int va_stride, va_n;          // position axes: velocity index along the axis
+    int periodic;
+    double *lam_g;                // velocity axes: cotangent of g (axis slice), or null
+    double dalpha_scale;          // tau / dv
+};
+
+template <typename T>
+__device__ __forceinline__ T dget(const T *tile, int C, int n, int j, int neg, int periodic, int t)
+{
+    if (periodic) {
+        j %= n;
+        if (j < 0) j += n;
+    } else if (j < 0 || j >= n) {
+        return T(0);
+    }
+    return tile[(neg ? n - 1 - j : j) * C + t];
+}
+
+template <typename T>
+__device__ __forceinline__ void dadd(T *tile, int C, int n, int j, int neg, int periodic, int t, T v)
+{
+    if (periodic) {
+        j %= n;
+        if (j < 0) j += n;
+    } else if (j < 0 || j >= n) {
+        return;
+    }
+    tile[(neg ? n - 1 - j : j) * C + t] += v;
+}
+
+// one line: F, LO tiles read-only, LI tile accumulates the input cotangent
+template <typename T>
+__device__ T line_adjoint(const T *F, const T *LO, T *LI, int C, int t, int n,
+                          const LineCoef<T> cf, int periodic)
+{
+    const int neg = cf.code & 1, s = cf.code >> 1;
+    const T c0 = cf.c0, c1 = cf.c1, c2 = cf.c2;
+    const T beta = c0;
+    const T dc1 = (T(2) - T(6) * beta + T(3) * beta * beta) / T(6);
+    const T dc2 = (T(1) - T(3) * beta * beta) / T(6);
+    T finf = T(0);
+    int arg = 0;
+    for (int j = 0; j < n; ++j) {
+        const T v = dget(F, C, n, j, neg, 0, t);
+        if (v > finf) { finf = v; arg = j; }
+    }
+    for (int j = 0; j < n; ++j) LI[j * C + t] = T(0);
+    T lfinf = T(0), dbeta = T(0);
+    for (int j = 0; j < n; ++j) {
+        // f_j enters out_{j+s} directly, -phi_j enters out_{j+s}, +phi_j out_{j+s+1}
+        const T l1 = (periodic || j + s < n) ? dget(LO, C, n, j + s, neg, periodic, t) : T(0);
+        const T l2 = (periodic || j + s + 1 < n) ? dget(LO, C, n, j + s + 1, neg, periodic, t) : T(0);
+        dadd(LI, C, n, j, neg, periodic, t, l1);
+        const T mu = l2 - l1;
+        if (mu == T(0)) continue;
+        const T fm = dget(F, C, n, j - 1, neg, periodic, t);
+        const T f0 = dget(F, C, n, j, neg, periodic, t);
+        const T fp = dget(F, C, n, j + 1, neg, periodic, t);
+        T l0 = c0 * mu, lm = T(0), lp = T(0);
+        T ep, em;
+        // E+ arm
+        const T dp = fp - f0;
+        if (dp > T(0) && T(2) * f0 < dp) {
+            ep = T(2) * f0;
+            l0 += T(2) * c1 * mu;
+        } else if (dp < T(0) && -T(2) * (finf - f0) > dp) {
+            ep = -T(2) * (finf - f0);
+            l0 += T(2) * c1 * mu;
+            lfinf -= T(2) * c1 * mu;
+        } else {
+            ep = dp;
+            lp += c1 * mu;
+            l0 -= c1 * mu;
+        }
+        // E- arm
+        const T dm = f0 - fm;
+        if (dm > T(0) && T(2) * (finf - f0) < dm) {
+            em = T(2) * (finf - f0);
+            lfinf += T(2) * c2 * mu;
+            l0 -= T(2) * c2 * mu;
+        } else if (dm < T(0) && -T(2) * f0 > dm) {
+            em = -T(2) * f0;
+            l0 -= T(2) * c2 * mu;
+        } else {
+            em = dm;
+            l0 += c2 * mu;
+            lm -= c2 * mu;
+        }
+        dadd(LI, C, n, j, neg, periodic, t, l0);
+        if (lp != T(0)) dadd(LI, C, n, j + 1, neg, periodic, t, lp);
+        if (lm != T(0)) dadd(LI, C, n, j - 1, neg, periodic, t, lm);
+        dbeta += mu * (f0 + dc1 * ep + dc2 * em);
+    }
+    dadd(LI, C, n, arg, neg, 0, t, lfinf);
+    return neg ? -dbeta : dbeta;
+}
+
+// generic line-adjoint kernel: blockIdx.y selects the outer index (position
+// axes) or the spatial cell (velocity axes); threads take consecutive lines
+template <typename T>
+__global__ void __launch_bounds__(128) k_sweep_adjoint(AdjArgs<T> A, LineGeom g)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int C = blockDim.x;
+    const int n = g.n;
+    T *F = reinterpret_cast<T *>(smem_raw);
+    T *LO = F + n * C;
+    T *LI = LO + n * C;
+    __shared__ double red[32];
+    const int t = threadIdx.x;
+    const long long w = (long long)blockIdx.x * C + t;
+    const bool active = w < g.nlines_inner;
+    long long base;
+    LineCoef<T> cf;
+    if (g.axis < 3) {
+        const int o = blockIdx.y;
+        const long long cell0 = (long long)(o / g.od) * g.m1 + (long long)(o % g.od) * g.m2;
+        base = cell0 * g.nvc + w;
+        if (active) cf = A.coef[(int)((w / A.va_stride) % A.va_n)];
+    } else {
+        const long long cell = blockIdx.y;
+        const long long voff = (w / g.wdiv) * g.wmul_hi + (w % g.wdiv) * g.wmul_lo;
+        base = cell * g.nvc + voff;
+        cf = A.coef[cell * 3 + (g.axis - 3)];
+    }
+    for (int j = 0; j < n; ++j) {
+        F[j * C + t] = active ? A.fin[base + j * g.stride] : T(0);
+        LO[j * C + t] = active ? A.lam[base + j * g.stride] : T(0);
+    }
+    double da = 0.0;
+    if (active) {
+        da = (double)line_adjoint<T>(F, LO, LI, C, t, n, cf, A.periodic);
+        for (int j = 0; j < n; ++j) A.lam[base + j * g.stride] = LI[j * C + t];
+    }
+    if (A.lam_g) {
+        da = block_sum(da, red);
+        if (t == 0 && da != 0.0) atomicAdd(A.lam_g + blockIdx.y, da * A.dalpha_scale);
+    }
+}
+
+// lam_phi (FFT grid) = transpose of the central-difference force applied to
+// lam_g (box): lam_phi[p] = sum_a c_a[p - e_a] - c_a[p + e_a],
+// c_a = -lam_g_a / (2 dx_a), zero outside the box
+__global__ void k_force_adjoint(const double *__restrict__ lam_g, double *__restrict__ lam_phi,
+                                int n0, int n1, int n2, int f0, int f1, int f2, double h0,
+                                double h1, double h2)
+{
+    const long long nf = (long long)f0 * f1 * f2;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nf) return;
+    const long long np = (long long)n0 * n1 * n2;
+    const int k = (int)(t % f2), j = (int)((t / f2) % f1), i = (int)(t / ((long long)f1 * f2));
+    auto c = [&](int a, int ii, int jj, int kk) -> double {
+        ii = (ii + f0) % f0;
+        jj = (jj + f1) % f1;
+        kk = (kk + f2) % f2;
+        if (ii >= n0 || jj >= n1 || kk >= n2) return 0.0;
+        const double h = a == 0 ? h0 : (a == 1 ? h1 : h2);
+        return -lam_g[a * np + ((long long)ii * n1 + jj) * n2 + kk] / (2.0 * h);
+    };
+    double v = c(0, i - 1, j, k) - c(0, i + 1, j, k);
+    v += c(1, i, j - 1, k) - c(1, i, j + 1, k);
+    v += c(2, i, j, k - 1) - c(2, i, j, k + 1);
+    lam_phi[t] = v;
+}
+
+__global__ void k_real_to_complex(const double *__restrict__ in, double2 *__restrict__ out,
+                                  long long n)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) out[t] = make_double2(in[t], 0.0);
+}
+
+// lam_f += dvol_v * lam_rho[cell] (lam_rho read from the box part of the
+// real part of cbuf)
+template <typename T>
+__global__ void k_broadcast_add(T *__restrict__ lam_f, const double2 *__restrict__ cbuf,
+                                long long nvc, int n1, int n2, int f1, int f2, double dvol_v,
+                                long long ncells)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ncells) return;
+    const long long cell = t / nvc;
+    const int k = (int)(cell % n2), j = (int)((cell / n2) % n1), i = (int)(cell / ((long long)n1 * n2));
+    const double v = cbuf[((long long)i * f1 + j) * f2 + k].x * dvol_v;
+    lam_f[t] = (T)((double)lam_f[t] + v);
+}
+
+// lam_f = scale * w[cell] broadcast over velocity, w = phi (kind 0) or
+// rho - target (kind 1)
+template <typename T>
+__global__ void k_functional_grad(T *__restrict__ lam_f, const double *__restrict__ phi,
+                                  const double *__restrict__ rho, const double *__restrict__ target,
+                                  int kind, long long nvc, int n1, int n2, int f1, int f2,
+                                  double scale, long long ncells)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ncells) return;
+    const long long cell = t / nvc;
+    double w;
+    if (kind == 0) {
+        const int k = (int)(cell % n2), j = (int)((cell / n2) % n1), i = (int)(cell / ((long long)n1 * n2));
+        w = phi[((long long)i * f1 + j) * f2 + k];
+    } else {
+        w = rho[cell] - target[cell];
+    }
+    lam_f[t] = (T)(w * scale);
+}
+
+// sum (rho - target)^2 (compensated), one CTA
+__global__ void k_misfit(const double *__restrict__ rho, const double *__restrict__ target,
+                         long long np, double *out)
+{
+    __shared__ Acc<double> red[32];
+    Acc<double> a;
+    for (long long t = threadIdx.x; t < np; t += blockDim.x) {
+        const double r = rho[t] - target[t];
+        a.add(r * r);
+    }
+    a = block_merge(a, red);
+    if (threadIdx.x == 0) out[0] = a.value();
+}
+
+template <typename T>
+cudaError_t sweep_adjoint_t(vp_ctx *c, const T *fin, T *lam, int axis, const LineCoef<T> *coef,
+                            double *lam_g, double dalpha_scale)
+{
+    LineGeom g;
+    AdjArgs<T> A;
+    g.axis = axis;
+    g.nvc = c->nvc;
+    A.fin = fin;
+    A.lam = lam;
+    A.lam_g = nullptr;
+    A.dalpha_scale = 0.0;
+    const int C = 128;
+    dim3 grid;
+    if (axis < 3) {
+        g.n = c->n[axis];
+        if (axis == 0) { g.cell_stride = (long long)c->n[1] * c->n[2]; g.od = 1; g.m1 = 1; g.m2 = 0; }
+        else if (axis == 1) { g.cell_stride = c->n[2]; g.od = c->n[2]; g.m1 = (long long)c->n[1] * c->n[2]; g.m2 = 1; }
+        else { g.cell_stride = 1; g.od = 1; g.m1 = c->n[2]; g.m2 = 0; }
+        g.stride = g.cell_stride * c->nvc;
+        g.nlines_inner = c->nvc;
+        A.coef = coef + (size_t)axis * c->maxnv;
+        A.va_stride = axis == 0 ? c->nv[1] * c->nv[2] : (axis == 1 ? c->nv[2] : 1);
+        A.va_n = c->nv[axis];
+        A.periodic = c->periodic_space;
+        grid = dim3((unsigned)((c->nvc + C - 1) / C), (unsigned)(c->np / g.n));
+    } else {
+        const int va = axis - 3;
+        const int nx = c->nv[0], ny = c->nv[1], nz = c->nv[2];
+        g.n = c->nv[va];
+        if (va == 0) { g.stride = (long long)ny * nz; g.wdiv = nz; g.wmul_hi = nz; g.wmul_lo = 1; g.nlines_inner = (long long)ny * nz; }
+        else if (va == 1) { g.stride = nz; g.wdiv = nz; g.wmul_hi = ny * nz; g.wmul_lo = 1; g.nlines_inner = (long long)nx * nz; }
+        else { g.stride = 1; g.wdiv = 1; g.wmul_hi = nz; g.wmul_lo = 0; g.nlines_inner = (long long)nx * ny; }
+        A.coef = coef;
+        A.va_stride = 1;
+        A.va_n = 1;
+        A.periodic = 0;
+        A.lam_g = lam_g ? lam_g + (size_t)va * c->np : nullptr;
+        A.dalpha_scale = dalpha_scale;
+        grid = dim3((unsigned)((g.nlines_inner + C - 1) / C), (unsigned)c->np);
+    }
+    const size_t smem = 3 * (size_t)g.n * C * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_adjoint<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_sweep_adjoint<T><<<grid, C, smem, c->stream>>>(A, g);
+    return cudaGetLastError();
+}
+
+inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+#define TRY(x)                      \
+    do {                            \
+        int _r = (x);               \
+        if (_r != VP_OK) return _r; \
+    } while (0)
+
+int ensure_adjoint_scratch(vp_ctx *c)
+{
+    if (c->adj_states) return VP_OK;
+    const size_t bytes = (size_t)c->ncells * c->esize;
+    c->adj_nstates = 9;
+    c->adj_states = (void **)calloc(9, sizeof(void *));
+    if (!c->adj_states) return VP_ERR_OOM;
+    for (int i = 0; i < 9; ++i)
+        if (cudaMalloc(&c->adj_states[i], bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return VP_ERR_OOM;
+        }
+    const size_t cs = c->isdouble ? sizeof(LineCoef<double>) : sizeof(LineCoef<float>);
+    if (cudaMalloc(&c->adj_f, cs * 3 * c->np) != cudaSuccess ||   // K1 table of the replay
+        cudaMalloc((void **)&c->adj_g, sizeof(double) * 3 * c->np) != cudaSuccess ||
+        cudaMalloc((void **)&c->adj_lg, sizeof(double) * 3 * c->np) != cudaSuccess ||
+        cudaMalloc((void **)&c->adj_tmp, sizeof(double) * c->nfft) != cudaSuccess) {
+        cudaGetLastError();
+        return VP_ERR_OOM;
+    }
+    return VP_OK;
+}
+
+// scalar on the device used as the replay's tau
+__global__ void k_set(double *p, double v) { *p = v; }
+
+}  // namespace
+
+cudaError_t launch_drift_adjoint(vp_ctx *c, const void *fin, void *lam, int axis, const void *coef)
+{
+    if (c->isdouble)
+        return sweep_adjoint_t<double>(c, (const double *)fin, (double *)lam, axis,
+                                       (const LineCoef<double> *)coef, nullptr, 0.0);
+    return sweep_adjoint_t<float>(c, (const float *)fin, (float *)lam, axis,
+                                  (const LineCoef<float> *)coef, nullptr, 0.0);
+}
+
+cudaError_t launch_kick_adjoint(vp_ctx *c, const void *fin, void *lam, int vaxis, const void *coef,
+                                double tau, double *lam_g)
+{
+    const double scale = tau / c->dv[vaxis];
+    if (c->isdouble)
+        return sweep_adjoint_t<double>(c, (const double *)fin, (double *)lam, 3 + vaxis,
+                                       (const LineCoef<double> *)coef, lam_g, scale);
+    return sweep_adjoint_t<float>(c, (const float *)fin, (float *)lam, 3 + vaxis,
+                                  (const LineCoef<float> *)coef, lam_g, scale);
+}
+
+// lam_f += R^T P^T F^T lam_g
+cudaError_t launch_field_adjoint(vp_ctx *c, const double *lam_g, void *lam_f)
+{
+    const int T = 256;
+    double *lam_phi = c->phi;   // scratch: the stored potential is recomputed by the next solve
+    k_force_adjoint<<<nblk(c->nfft, T), T, 0, c->stream>>>(lam_g, lam_phi, c->n[0], c->n[1], c->n[2],
+                                                           c->fn[0], c->fn[1], c->fn[2], c->dx[0],
+                                                           c->dx[1], c->dx[2]);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_real_to_complex<<<nblk(c->nfft, T), T, 0, c->stream>>>(lam_phi, c->cbuf, c->nfft);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    for (int a = 2; a >= 0; --a)
+        if ((e = launch_fft(c, c->cbuf, a, 0)) != cudaSuccess) return e;
+    if ((e = launch_green_mul(c)) != cudaSuccess) return e;
+    for (int a = 0; a < 3; ++a)
+        if ((e = launch_fft(c, c->cbuf, a, 1)) != cudaSuccess) return e;
+    if (c->isdouble)
+        k_broadcast_add<double><<<nblk(c->ncells, T), T, 0, c->stream>>>(
+            (double *)lam_f, c->cbuf, c->nvc, c->n[1], c->n[2], c->fn[1], c->fn[2], c->dvol_v, c->ncells);
+    else
+        k_broadcast_add<float><<<nblk(c->ncells, T), T, 0, c->stream>>>(
+            (float *)lam_f, c->cbuf, c->nvc, c->n[1], c->n[2], c->fn[1], c->fn[2], c->dvol_v, c->ncells);
+    return cudaGetLastError();
+}
+
 extern "C" {
 
-int vp_adjoint_step(vp_ctx *c, const void *f_start, const double *g_start, double *lambda_f,
+int vp_sweep_adjoint(vp_ctx *c, int axis, double tau, const void *f_in, void *lambda,
+                     double *lambda_g)
+{
+    if (!c || !f_in || !lambda || axis < 0 || axis > 5 || !isfinite(tau)) return VP_ERR_ARG;
+    double *tau_ptr = &c->sc->pad[3];
+    k_set<<<1, 1, 0, c->stream>>>(tau_ptr, tau);
+    VP_CUDA_TRY(cudaGetLastError());
+    if (axis < 3) {
+        VP_CUDA_TRY(launch_coef_drift(c, tau_ptr, 1.0, c->coef_drift));
+        VP_CUDA_TRY(launch_drift_adjoint(c, f_in, lambda, axis, c->coef_drift));
+    } else {
+        VP_CUDA_TRY(launch_coef_kick(c, c->g, tau_ptr, 1.0, c->coef_kick1));
+        VP_CUDA_TRY(launch_kick_adjoint(c, f_in, lambda, axis - 3, c->coef_kick1, tau, lambda_g));
+    }
+    return VP_OK;
+}
+
+int vp_field_adjoint(vp_ctx *c, const double *lambda_g, void *lambda_f)
+{
+    if (!c || !lambda_g || !lambda_f) return VP_ERR_ARG;
+    VP_CUDA_TRY(launch_field_adjoint(c, lambda_g, lambda_f));
+    return VP_OK;
+}
+
+int vp_functional(vp_ctx *c, int kind, const double *target, void *lambda_f, double *J_out)
+{
+    if (!c || !lambda_f || (kind != 0 && kind != 1) || (kind == 1 && !target)) return VP_ERR_ARG;
+    const int T = 256;
+    VP_CUDA_TRY(launch_density(c, c->f, c->rho2));
+    double *sums = c->red + 2 * c->np;
+    if (kind == 0) {
+        VP_CUDA_TRY(launch_field_solve(c, c->rho2, nullptr));
+        VP_CUDA_TRY(launch_dot_rho_phi(c, c->rho2, sums));
+    } else {
+        k_misfit<<<1, 1024, 0, c->stream>>>(c->rho2, target, c->np, sums);
+        VP_CUDA_TRY(cudaGetLastError());
+    }
+    const double scale = c->dvol_v * c->dvol_x;
+    if (c->isdouble)
+        k_functional_grad<double><<<nblk(c->ncells, T), T, 0, c->stream>>>(
+            (double *)lambda_f, c->phi, c->rho2, target, kind, c->nvc, c->n[1], c->n[2], c->fn[1],
+            c->fn[2], scale, c->ncells);
+    else
+        k_functional_grad<float><<<nblk(c->ncells, T), T, 0, c->stream>>>(
+            (float *)lambda_f, c->phi, c->rho2, target, kind, c->nvc, c->n[1], c->n[2], c->fn[1],
+            c->fn[2], scale, c->ncells);
+    VP_CUDA_TRY(cudaGetLastError());
+    double h;
+    VP_CUDA_TRY(cudaMemcpyAsync(&h, sums, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    VP_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (J_out) *J_out = 0.5 * h * c->dvol_x;
+    return VP_OK;
+}
+
+int vp_adjoint_step(vp_ctx *c, const void *f_start, const double *g_start, void *lambda_f,
                     double *lambda_g)
 {
-    (void)c; (void)f_start; (void)g_start; (void)lambda_f; (void)lambda_g;
-    return VP_ERR_UNSUPPORTED;
-}
-
-int vp_field_adjoint(vp_ctx *c, const double *lambda_g, double *lambda_f)
-{
-    (void)c; (void)lambda_g; (void)lambda_f;
-    return VP_ERR_UNSUPPORTED;
-}
-
-int vp_functional(vp_ctx *c, int kind, const double *target, double *lambda_f, double *J_out)
-{
-    (void)c; (void)kind; (void)target; (void)lambda_f; (void)J_out;
-    return VP_ERR_UNSUPPORTED;
+    if (!c || !f_start || !g_start || !lambda_f || !lambda_g) return VP_ERR_ARG;
+    if (!(c->cfg.dt_fixed > 0.0)) return VP_ERR_STATE;
+    TRY(ensure_adjoint_scratch(c));
+    const double dt = c->cfg.dt_fixed;
+    const size_t bytes = (size_t)c->ncells * c->esize;
+    void **S = c->adj_states;
+    double *tau_ptr = &c->sc->pad[2];
+    k_set<<<1, 1, 0, c->stream>>>(tau_ptr, dt);
+    VP_CUDA_TRY(cudaGetLastError());
+    // tables of the replay: K1 from g^n, drift, K2 from the recomputed g^{n+1}
+    void *k1 = c->adj_f;
+    VP_CUDA_TRY(launch_coef_kick(c, g_start, tau_ptr, 0.5, k1));
+    VP_CUDA_TRY(launch_coef_drift(c, tau_ptr, 1.0, c->coef_drift));
+    // forward replay, keeping every sweep input S[0..8]
+    VP_CUDA_TRY(cudaMemcpyAsync(S[0], f_start, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    for (int k = 0; k < 8; ++k) {
+        VP_CUDA_TRY(cudaMemcpyAsync(S[k + 1], S[k], bytes, cudaMemcpyDeviceToDevice, c->stream));
+        if (k < 3) {
+            VP_CUDA_TRY(launch_kick(c, S[k + 1], k1, nullptr, 1, k));
+        } else if (k < 6) {
+            const int axis = 5 - k;                       // z, y, x
+            VP_CUDA_TRY(launch_drift(c, S[k + 1], axis, c->coef_drift, vp_drift_alpha_bound(c, dt),
+                                     nullptr));
+            if (k == 5) {
+                VP_CUDA_TRY(launch_density(c, S[6], c->rho2));
+                VP_CUDA_TRY(launch_field_solve(c, c->rho2, c->adj_g));
+                VP_CUDA_TRY(launch_coef_kick(c, c->adj_g, tau_ptr, 0.5, c->coef_kick2));
+            }
+        } else {
+            VP_CUDA_TRY(launch_kick(c, S[k + 1], c->coef_kick2, nullptr, 1, k - 6));
+        }
+    }
+    // K2 (vz, vy, vx) reversed; its g-cotangent is added to lambda_g^{n+1}
+    for (int va = 2; va >= 0; --va)
+        VP_CUDA_TRY(launch_kick_adjoint(c, S[6 + va], lambda_f, va, c->coef_kick2, 0.5 * dt, lambda_g));
+    // g^{n+1} = field(f_b)
+    VP_CUDA_TRY(launch_field_adjoint(c, lambda_g, lambda_f));
+    // drift x, y, z reversed
+    for (int k = 5; k >= 3; --k)
+        VP_CUDA_TRY(launch_drift_adjoint(c, S[k], lambda_f, 5 - k, c->coef_drift));
+    // K1 reversed; its g-cotangent is that of g^n
+    VP_CUDA_TRY(cudaMemsetAsync(lambda_g, 0, sizeof(double) * 3 * c->np, c->stream));
+    for (int va = 2; va >= 0; --va)
+        VP_CUDA_TRY(launch_kick_adjoint(c, S[va], lambda_f, va, k1, 0.5 * dt, lambda_g));
+    return VP_OK;
 }
 
 }  // extern "C"

@@ -157,9 +157,11 @@ int check_config(const vp_config *cfg)
     return VP_OK;
 }
 
+}  // namespace
+
 // host bound of |v tau / dx| over the drift tables: for the step, tau = dt,
-// which is either fixed or at most C dx_a / V^max_a on every axis
-double drift_alpha_bound(const vp_ctx *c, double tau)
+// which is either fixed or at most C dx_a / V^max_a on every axis (tau <= 0)
+double vp_drift_alpha_bound(const vp_ctx *c, double tau)
 {
     double m = 0.0;
     for (int a = 0; a < 3; ++a) {
@@ -177,9 +179,11 @@ double drift_alpha_bound(const vp_ctx *c, double tau)
     return m;
 }
 
+namespace {
+
 double step_alpha_bound(const vp_ctx *c)
 {
-    return drift_alpha_bound(c, c->cfg.dt_fixed > 0.0 ? c->cfg.dt_fixed : -1.0);
+    return vp_drift_alpha_bound(c, c->cfg.dt_fixed > 0.0 ? c->cfg.dt_fixed : -1.0);
 }
 
 int field_from_f(vp_ctx *c)
@@ -463,7 +467,7 @@ int vp_sweep(vp_ctx *c, int axis, double tau)
     VP_CUDA_TRY(cudaGetLastError());
     if (axis < 3) {
         VP_CUDA_TRY(launch_coef_drift(c, tau_ptr, 1.0, c->coef_drift));
-        VP_CUDA_TRY(launch_drift(c, c->f, axis, c->coef_drift, drift_alpha_bound(c, fabs(tau)),
+        VP_CUDA_TRY(launch_drift(c, c->f, axis, c->coef_drift, vp_drift_alpha_bound(c, fabs(tau)),
                                  nullptr));
     } else {
         VP_CUDA_TRY(launch_coef_kick(c, c->g, tau_ptr, 1.0, c->coef_kick1));

@@ -292,6 +292,12 @@ cudaError_t launch_field_solve(vp_ctx *c, const double *rho, double *g_out)
     return cudaSuccess;
 }
 
+cudaError_t launch_green_mul(vp_ctx *c)
+{
+    k_green_mul<<<blocks_for(c->nfft, 256), 256, 0, c->stream>>>(c->cbuf, c->ghat, c->nfft);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_copy_phi_box(vp_ctx *c, double *dst)
 {
     k_copy_box<<<blocks_for(c->np, 256), 256, 0, c->stream>>>(c->phi, dst, c->n[0], c->n[1],

@@ -138,12 +138,11 @@ cudaError_t launch_rho_finish(vp_ctx *c, const double *part, int nparts, double 
 int vp_fft_plan_axis(FFTAxis *a, int n);
 cudaError_t launch_fft(vp_ctx *c, double2 *data, int axis, int inverse);
 
-// adjoint
-cudaError_t launch_drift_adjoint(vp_ctx *c, const void *fin, double *lam, int axis,
-                                 const void *coef);
-cudaError_t launch_kick_adjoint(vp_ctx *c, const void *fin, double *lam, int vaxis,
-                                const void *coef, const double *g, double tau_factor,
-                                double *lam_g);
-cudaError_t launch_field_adjoint(vp_ctx *c, const double *lam_g, double *lam_f);
-cudaError_t launch_functional(vp_ctx *c, int kind, const double *rho, const double *target,
-                              double *lam_f);
+cudaError_t launch_green_mul(vp_ctx *c);
+double vp_drift_alpha_bound(const vp_ctx *c, double tau);
+
+// adjoint (vp_adjoint.cu)
+cudaError_t launch_drift_adjoint(vp_ctx *c, const void *fin, void *lam, int axis, const void *coef);
+cudaError_t launch_kick_adjoint(vp_ctx *c, const void *fin, void *lam, int vaxis, const void *coef,
+                                double tau, double *lam_g);
+cudaError_t launch_field_adjoint(vp_ctx *c, const double *lam_g, void *lam_f);

@@ -160,6 +160,11 @@ class VlasovPoisson:
         check(self.lib.vp_adjoint_step(self._ctx, _ptr(f_start), _ptr(g_start), _ptr(lam_f),
                                        _ptr(lam_g)), "vp_adjoint_step")
 
+    def sweep_adjoint(self, axis: int, tau: float, f_in: torch.Tensor, lam: torch.Tensor,
+                      lam_g: Optional[torch.Tensor] = None) -> None:
+        check(self.lib.vp_sweep_adjoint(self._ctx, int(axis), float(tau), _ptr(f_in), _ptr(lam),
+                                        _ptr(lam_g)), "vp_sweep_adjoint")
+
     def field_adjoint(self, lam_g: torch.Tensor, lam_f: torch.Tensor) -> None:
         check(self.lib.vp_field_adjoint(self._ctx, _ptr(lam_g), _ptr(lam_f)), "vp_field_adjoint")
 

@@ -1,0 +1,158 @@
+"""GPU discrete adjoint against the FP64 oracle's adjoint (same frozen-branch
+rules) and against central finite differences of the GPU forward map."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytestmark = pytest.mark.skip(reason="needs a CUDA GPU")
+
+from oracle import vp_oracle as O  # noqa: E402
+from paper_1206_6152_gb300 import inputs as I  # noqa: E402
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1206_6152_gb300 import build as B
+    B.build()
+
+
+def gpu_sim(w, f_np, dtype=None):
+    from paper_1206_6152_gb300.vlasov import VlasovPoisson, config_of
+    tdt = dtype or (torch.float32 if w.dtype == "f32" else torch.float64)
+    f = torch.from_numpy(np.ascontiguousarray(f_np)).to(DEV, tdt)
+    return VlasovPoisson(config_of(w, tdt), f), f
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("space_bc", ["periodic", "outflow"])
+def test_sweep_adjoint_matches_oracle(space_bc):
+    w = I.small_maxwell(n=(6, 5, 4), nv=(8, 7, 6), dtype="f64", amp=0.3, space_bc=space_bc)
+    grid = O.Grid.of(w)
+    rng = np.random.default_rng(21)
+    f0 = I.initial_condition(w) * (1 + 0.5 * rng.random(w.shape))     # tie free
+    acc = rng.normal(size=(3,) + w.n) * 3
+    sim, f = gpu_sim(w, f0)
+    sim.set_accel(torch.from_numpy(acc))
+    per = space_bc == "periodic"
+    for axis in range(6):
+        for tau in (0.017, -0.023, 0.31):
+            lam0 = rng.normal(size=w.shape)
+            fin = torch.from_numpy(f0).to(DEV)
+            lam = torch.from_numpy(lam0).to(DEV)
+            lg = torch.zeros((3,) + w.n, dtype=torch.float64, device=DEV)
+            sim.sweep_adjoint(axis, tau, fin, lam, lg)
+            ref = lam0.copy()
+            ds = np.zeros(int(np.prod(w.n)))
+            if axis < 3:
+                O.sweep_adjoint(f0, ref, axis, grid.vc(axis), tau, grid.dx[axis], per, None)
+            else:
+                O.sweep_adjoint(f0, ref, axis, acc[axis - 3], tau, grid.dv[axis - 3], False, ds)
+            got = lam.cpu().numpy()
+            assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max(), (axis, tau)
+            if axis >= 3:
+                gg = lg.cpu().numpy()[axis - 3].reshape(-1)
+                assert np.abs(gg - ds).max() <= 1e-10 * max(np.abs(ds).max(), 1e-300), (axis, tau)
+    sim.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("bc", ["periodic", "isolated"])
+def test_adjoint_step_matches_oracle(bc):
+    w = I.small_maxwell(n=(6, 5, 4), nv=(8, 7, 6), dtype="f64", amp=0.2, G=20.0)
+    w = w.replace(dt_fixed=0.01)
+    if bc == "isolated":
+        w = w.replace(box_lo=(-0.3, -0.25, -0.2), box_hi=(0.3, 0.25, 0.2), poisson_bc="isolated",
+                      space_bc="outflow")
+    grid = O.Grid.of(w)
+    rng = np.random.default_rng(3)
+    f0 = I.initial_condition(w) * (1 + 0.2 * rng.random(w.shape))
+    sim, f = gpu_sim(w, f0)
+    g0 = sim.field()[2]
+    lam_f = torch.from_numpy(rng.normal(size=w.shape)).to(DEV)
+    lam_g = torch.from_numpy(rng.normal(size=(3,) + w.n)).to(DEV)
+    lf0, lg0 = lam_f.cpu().numpy(), lam_g.cpu().numpy()
+    sim.adjoint_step(torch.from_numpy(f0).to(DEV), g0, lam_f, lam_g)
+    osim = O.Simulation(f0, grid, O.Params.of(w))
+    rf, rg = O.adjoint_step(osim, f0, osim.g, lf0, lg0)
+    assert np.abs(g0.cpu().numpy() - osim.g).max() <= 1e-11 * np.abs(osim.g).max()
+    got_f, got_g = lam_f.cpu().numpy(), lam_g.cpu().numpy()
+    assert np.abs(got_f - rf).max() <= 1e-9 * np.abs(rf).max()
+    assert np.abs(got_g - rg).max() <= 1e-9 * np.abs(rg).max()
+    sim.close()
+
+
+def _mode_f0(w, amps, dtype):
+    """f0(A) = rho_bar (1 + sum_m A_m cos(k_m.x + th_m)) M(v), in torch."""
+    fields = torch.from_numpy(I.mode_fields(w)).to(DEV)
+    mv = torch.from_numpy(I.maxwellian_v(w)).to(DEV)
+    rho = w.rho_bar * (1 + torch.tensordot(amps.to(torch.float64), fields, dims=1))
+    return (rho[..., None, None, None] * mv).to(dtype).contiguous()
+
+
+def _J_of(sim, f0, nsteps, kind, target):
+    with torch.no_grad():
+        sim.f.copy_(f0)
+        sim.refresh_field()
+        sim.step(nsteps)
+        lam = torch.empty_like(sim.f)
+        return sim.functional(kind, lam, target)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("kind", [0, 1])
+def test_trajectory_gradient_fp64_matches_fd(kind):
+    from paper_1206_6152_gb300.adjoint import trajectory_functional
+    w = I.small_maxwell(n=(8, 6, 5), nv=(10, 8, 9), dtype="f64", amp=0.1, G=25.0)
+    w = w.replace(dt_fixed=0.008)
+    amps0 = torch.tensor([m[1] for m in w.modes], dtype=torch.float64, device=DEV)
+    sim, f = gpu_sim(w, np.zeros(w.shape))
+    target = None
+    if kind == 1:
+        target = torch.from_numpy(w.rho_bar * (1 + 0.05 * I.mode_fields(w)[0])).to(DEV)
+    nsteps = 6
+    amps = amps0.clone().requires_grad_(True)
+    J = trajectory_functional(_mode_f0(w, amps, torch.float64), sim, nsteps, every=4, kind=kind,
+                              target=target)
+    J.backward()
+    grad = amps.grad.cpu().numpy()
+    for m in range(len(w.modes)):
+        h = 1e-7
+        ap, am = amps0.clone(), amps0.clone()
+        ap[m] += h
+        am[m] -= h
+        fd = (_J_of(sim, _mode_f0(w, ap, torch.float64), nsteps, kind, target)
+              - _J_of(sim, _mode_f0(w, am, torch.float64), nsteps, kind, target)) / (2 * h)
+        assert grad[m] == pytest.approx(fd, rel=1e-5, abs=1e-9 * abs(J.item())), m
+    sim.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.slow
+def test_jeans32_modes3_gradient_fp32_matches_fd():
+    """The 32^3 x 32^3 FP32 Jeans box with 3 seeded modes: gradient of the
+    final field energy w.r.t. the mode amplitudes through the adjoint with
+    checkpoints every 10 steps, against central differences (relative step
+    2e-2 of each amplitude; FP32 rounding noise is far below that)."""
+    from paper_1206_6152_gb300.adjoint import trajectory_functional
+    w = I.adjoint_c4()
+    nsteps = w.steps                     # 100 steps, checkpoints every 10
+    amps0 = torch.tensor([m[1] for m in w.modes], dtype=torch.float64, device=DEV)
+    sim, f = gpu_sim(w, np.zeros(w.shape, np.float32))
+    amps = amps0.clone().requires_grad_(True)
+    J = trajectory_functional(_mode_f0(w, amps, torch.float32), sim, nsteps, every=10, kind=0)
+    J.backward()
+    grad = amps.grad.cpu().numpy()
+    for m in range(len(w.modes)):
+        h = 2e-2 * float(amps0[m])
+        ap, am = amps0.clone(), amps0.clone()
+        ap[m] += h
+        am[m] -= h
+        fd = (_J_of(sim, _mode_f0(w, ap, torch.float32), nsteps, 0, None)
+              - _J_of(sim, _mode_f0(w, am, torch.float32), nsteps, 0, None)) / (2 * h)
+        assert grad[m] == pytest.approx(fd, rel=1e-3), (m, grad[m], fd)
+    sim.close()
