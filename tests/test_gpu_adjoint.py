@@ -136,8 +136,13 @@ def test_trajectory_gradient_fp64_matches_fd(kind):
 def test_jeans32_modes3_gradient_fp32_matches_fd():
     """The 32^3 x 32^3 FP32 Jeans box with 3 seeded modes: gradient of the
     final field energy w.r.t. the mode amplitudes through the adjoint with
-    checkpoints every 10 steps, against central differences (relative step
-    2e-2 of each amplitude; FP32 rounding noise is far below that)."""
+    checkpoints every 10 steps, against central differences.  In the linear
+    regime J is quadratic in the amplitudes, so a central difference is exact
+    for any step; the step (10% of each amplitude) keeps the FP32 rounding of
+    J below the difference.  The Landau-damped mode (k/k_J = 1.5) has, after
+    100 steps, a gradient ~250 times smaller than the growing ones, below the
+    FP32 resolution of a difference quotient of J; errors are therefore
+    measured against the largest gradient component."""
     from paper_1206_6152_gb300.adjoint import trajectory_functional
     w = I.adjoint_c4()
     nsteps = w.steps                     # 100 steps, checkpoints every 10
@@ -147,12 +152,19 @@ def test_jeans32_modes3_gradient_fp32_matches_fd():
     J = trajectory_functional(_mode_f0(w, amps, torch.float32), sim, nsteps, every=10, kind=0)
     J.backward()
     grad = amps.grad.cpu().numpy()
+    fds = []
     for m in range(len(w.modes)):
-        h = 2e-2 * float(amps0[m])
+        h = 0.1 * float(amps0[m])
         ap, am = amps0.clone(), amps0.clone()
         ap[m] += h
         am[m] -= h
-        fd = (_J_of(sim, _mode_f0(w, ap, torch.float32), nsteps, 0, None)
-              - _J_of(sim, _mode_f0(w, am, torch.float32), nsteps, 0, None)) / (2 * h)
-        assert grad[m] == pytest.approx(fd, rel=1e-3), (m, grad[m], fd)
+        fds.append((_J_of(sim, _mode_f0(w, ap, torch.float32), nsteps, 0, None)
+                    - _J_of(sim, _mode_f0(w, am, torch.float32), nsteps, 0, None)) / (2 * h))
+    fds = np.array(fds)
+    assert np.abs(grad - fds).max() <= 1e-3 * np.abs(fds).max(), (grad, fds)
+    # directional derivative along the amplitude vector itself
+    eps = 0.05
+    fd = (_J_of(sim, _mode_f0(w, amps0 * (1 + eps), torch.float32), nsteps, 0, None)
+          - _J_of(sim, _mode_f0(w, amps0 * (1 - eps), torch.float32), nsteps, 0, None)) / (2 * eps)
+    assert float(np.dot(grad, amps0.cpu().numpy())) == pytest.approx(fd, rel=1e-3)
     sim.close()
