@@ -188,6 +188,33 @@ int vp_field_adjoint(vp_ctx *ctx, const double *lambda_g, void *lambda_f);
 int vp_functional(vp_ctx *ctx, int kind, const double *target, void *lambda_f,
                   double *J_out);
 
+/* Allocation-free moments (the paper has no counterpart; this is a service
+ * for callers that cannot allocate device memory when they need the
+ * diagnostic -- e.g. code inside a CUDA stream capture, which an allocation
+ * would break, or an application whose device memory is handed out by its
+ * own allocator and fixed after start-up).  No context is needed and no
+ * device memory is allocated or freed.
+ *   f_dev:    distribution function (device, layout above), dtype 0 float /
+ *             1 double, spatial grid n[3], velocity grid nv[3] on
+ *             [vlo, vhi) (host arrays)
+ *   sums_dev: output, 2 doubles on the device: sums_dev[0] = sum f and
+ *             sums_dev[1] = sum f |v|^2 over all cells (cell-centre v,
+ *             compensated sums; multiply by dV = dx^3 dv^3, and by 1/2 for
+ *             K, to get the M and K of vp_energy)
+ * Asynchronous on cuda_stream.  The per-cell partial sums live in one
+ * static device array of the library sized for at most 262144 spatial cells
+ * (64^3; 4 MiB, held on every GPU that loads the library until the process
+ * exits); larger grids return VP_ERR_UNSUPPORTED.  The first call on each
+ * device looks up that array's device address (cudaGetSymbolAddress) and
+ * caches it, so make the first call on a device before any stream capture.
+ * Every call writes all the partials it reads, so no state carries over
+ * between calls, but all calls share the one array: calls that overlap on
+ * the GPU (different streams, or a stream and a graph) race and must be
+ * serialised by the caller. */
+int vp_moments_noalloc(const void *f_dev, int dtype, const int n[3], const int nv[3],
+                       const double vlo[3], const double vhi[3], double *sums_dev,
+                       void *cuda_stream);
+
 /* Releases everything the context owns (not f). */
 void vp_destroy(vp_ctx *ctx);
 

@@ -20,7 +20,7 @@ EXPORTS = (
     "vp_init", "vp_set_distribution", "vp_refresh_field", "vp_step", "vp_sweep",
     "vp_moments", "vp_get_field", "vp_set_accel", "vp_energy", "vp_time", "vp_step_host",
     "vp_adjoint_step", "vp_field_adjoint", "vp_functional", "vp_destroy", "vp_error_string",
-    "vp_profile_step", "vp_stats", "vp_sweep_adjoint",
+    "vp_profile_step", "vp_stats", "vp_sweep_adjoint", "vp_moments_noalloc",
 )
 PROFILE_SLOTS = 8
 PROFILE_NAMES = ("kick6", "drift_z", "drift_y", "drift_x", "density", "field", "tables", "step")
@@ -81,6 +81,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "vp_adjoint_step": (i, [vp, vp, vp, vp, vp]),
             "vp_field_adjoint": (i, [vp, vp, vp]),
             "vp_sweep_adjoint": (i, [vp, i, d, vp, vp, vp]),
+            "vp_moments_noalloc": (i, [vp, i, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       dp, dp, vp, vp]),
             "vp_functional": (i, [vp, i, vp, vp, dp]),
             "vp_destroy": (None, [vp]),
             "vp_error_string": (ctypes.c_char_p, [i]),
