@@ -45,6 +45,7 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--profile-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--adjoint-steps", type=int, default=3)
     p.add_argument("--cpu-sample", type=float, default=1.0 / 64)
     return p.parse_args()
 
@@ -322,6 +323,12 @@ def run_ours(args, ranks: Ranks):
     sim.close()
     del f
 
+    # adjoint / forward time per step on the fixed-dt workload of the same
+    # grid (the adjoint step replays its forward step, then reverses it)
+    adjoint = None
+    if args.adjoint_steps > 0:
+        adjoint = time_adjoint(args, dev, stream)
+
     cpu = None
     if ranks.rank == 0 and ranks.world == 1 and not args.no_cpu_baseline:
         rate, full_s, desc = oracle_step_rate(w, f0, args.cpu_sample)
@@ -338,9 +345,45 @@ def run_ours(args, ranks: Ranks):
                    "l2": "inputs larger than L2 (f is %.1f GB)" % (w.cells * esize / 1e9),
                    "parallelism": "replicas" if ranks.world > 1 else "single GPU"},
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
-        "cpu_baseline": cpu,
+        "adjoint": adjoint, "cpu_baseline": cpu,
     }
     return out
+
+
+def time_adjoint(args, dev, stream):
+    import torch
+    from paper_1206_6152_gb300 import inputs as I
+    from paper_1206_6152_gb300.vlasov import VlasovPoisson, config_of
+    w = I.adjoint_c4()
+    f = torch.from_numpy(I.initial_condition(w)).to(dev)
+    sim = VlasovPoisson(config_of(w), f, stream)
+    k = args.adjoint_steps
+    sim.step(3)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(k)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    fwd = e0.elapsed_time(e1) / k
+    f_start = f.clone()
+    g_start = sim.field()[2]
+    lam_f = torch.zeros_like(f)
+    lam_g = torch.zeros_like(g_start)
+    sim.functional(0, lam_f)
+    sim.adjoint_step(f_start, g_start, lam_f, lam_g)       # allocates its scratch
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(k):
+        sim.adjoint_step(f_start, g_start, lam_f, lam_g)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    adj = e0.elapsed_time(e1) / k
+    sim.close()
+    return {"workload": w.name, "forward_ms_per_step": round(fwd, 3),
+            "adjoint_ms_per_step": round(adj, 3), "ratio": round(adj / fwd, 3),
+            "note": "adjoint step = replay of its forward step (9 sweeps, kept) + 9 adjoint sweeps "
+                    "+ field adjoint; segment recompute of the checkpoints not included"}
 
 
 def run_reference(args, ranks: Ranks):

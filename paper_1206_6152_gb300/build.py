@@ -1,7 +1,7 @@
 """Builds the CUDA library libvp.so in-tree for sm_103a.
 
 Each .cu file under csrc/ is compiled by nvcc in parallel
-(-gencode arch=compute_103a,code=sm_103a, -O3, -lineinfo) and the objects are
+(-gencode arch=compute_103a,code=sm_103a, -O3, -lineinfo, -ftz=true) and the objects are
 linked into paper_1206_6152_gb300/libvp.so with the CUDA runtime linked
 statically.  Object files go to paper_1206_6152_gb300/_build/.
 """
@@ -39,8 +39,19 @@ def _stale(obj: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+FLAGS_STAMP = os.path.join(BUILD, "flags.txt")
+FLAGS = "-O3 -lineinfo -std=c++17 -ftz=true"
+
+
 def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
+    # FP32 denormals are flushed to zero: the positivity argument of the
+    # saturating-multiply corrector relies on relative rounding, which
+    # denormals do not have
+    if not os.path.exists(FLAGS_STAMP) or open(FLAGS_STAMP).read() != FLAGS:
+        force = True
+        with open(FLAGS_STAMP, "w") as fh:
+            fh.write(FLAGS)
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".cuh")]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "vp.h"))
     srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
@@ -49,8 +60,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
         src = os.path.join(CSRC, s)
         obj = os.path.join(BUILD, s.replace(".cu", ".o"))
         if force or _stale(obj, [src] + headers):
-            cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                   "-c", src, "-o", obj]
+            cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-ftz=true", "-Xcompiler",
+                   "-fPIC", "-c", src, "-o", obj]
             jobs.append((cmd, obj))
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:

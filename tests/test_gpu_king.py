@@ -1,0 +1,98 @@
+"""Isolated King sphere (Test 5, Sec. 3.5): Hockney isolated Poisson, outflow
+in position and velocity.
+
+* small grid: GPU against the FP64 oracle for a few steps (same IC, same
+  virial scale);
+* the 64^3 x 32^3 workload (W0 = 6, velocity bound 3 sigma_c): virial ratio
+  1 after the renormalisation of Sec. 3.5, and over one dynamical time
+  T = (G M / r0^3)^{-1/2} the paper's figures -- total energy within 1%,
+  mass bookkeeping (M + outflow = M0) exact, f >= 0 -- and a stationary
+  enclosed-mass profile.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytestmark = pytest.mark.skip(reason="needs a CUDA GPU")
+
+from oracle import vp_oracle as O  # noqa: E402
+from paper_1206_6152_gb300 import inputs as I  # noqa: E402
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1206_6152_gb300 import build as B
+    B.build()
+
+
+def gpu_sim(w, f_np, dtype):
+    from paper_1206_6152_gb300.vlasov import VlasovPoisson, config_of
+    f = torch.from_numpy(np.ascontiguousarray(f_np)).to(DEV, dtype)
+    return VlasovPoisson(config_of(w, dtype), f), f
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-11), (torch.float32, 1e-5)])
+def test_small_king_matches_oracle(dtype, tol):
+    w = I.king_c3(n=16, nv=16)
+    f0 = I.initial_condition(w, np.float64)
+    grid = O.Grid.of(w)
+    osim = O.Simulation(f0, grid, O.Params.of(w))
+    M, K, U, E, _ = osim.energy()
+    scale = 2 * K / abs(U)                     # virial ratio 2K/|U| = 1 (U ~ M^2)
+    f0 = f0 * scale
+    osim = O.Simulation(f0, grid, O.Params.of(w))
+    sim, f = gpu_sim(w, f0.astype(np.float32) if dtype == torch.float32 else f0, dtype)
+    e = sim.energy()
+    assert 2 * e["K"] / abs(e["U"]) == pytest.approx(1.0, rel=1e-6)
+    t = sim.step(3, sync=True)
+    osim.step(3)
+    got = f.cpu().numpy().astype(np.float64)
+    assert abs(t - osim.t) <= 1e-6 * osim.t
+    assert np.abs(got - osim.f).sum() / np.abs(osim.f).sum() <= tol
+    assert got.min() >= 0.0
+    e1, r1 = sim.energy(), osim.energy()
+    assert e1["M_out"] == pytest.approx(r1[4], rel=1e-4, abs=1e-12 * r1[0])
+    assert e1["E"] == pytest.approx(r1[3], rel=1e-5)
+    sim.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.slow
+def test_king64x32_one_dynamical_time():
+    w = I.king_c3()
+    f0 = I.initial_condition(w)
+    sim, f = gpu_sim(w, f0, torch.float32)
+    del f0
+    e = sim.energy()
+    f.mul_(2 * e["K"] / abs(e["U"]))
+    sim.refresh_field()
+    e0 = sim.energy()
+    assert 2 * e0["K"] / abs(e0["U"]) == pytest.approx(1.0, rel=1e-6)
+    M0 = e0["M"]
+    T = (w.G * M0) ** -0.5                      # r0 = 1
+    xs = [torch.from_numpy(w.centres_x(a)).to(DEV) for a in range(3)]
+    r = torch.sqrt(xs[0][:, None, None] ** 2 + xs[1][None, :, None] ** 2
+                   + xs[2][None, None, :] ** 2).reshape(-1)
+    edges = torch.linspace(0, 12, 25, device=DEV, dtype=torch.float64)
+    idx = torch.bucketize(r, edges)
+
+    def enclosed_mass():
+        rho = sim.density().reshape(-1)
+        m = torch.zeros(len(edges) + 1, dtype=torch.float64, device=DEV).index_add_(0, idx, rho)
+        return np.cumsum(m.cpu().numpy()) * float(np.prod(w.dx))
+
+    m0 = enclosed_mass()
+    t = 0.0
+    while t < T:
+        t = sim.step(1, sync=True)
+    e1 = sim.energy()
+    assert float(f.min()) >= 0.0
+    assert abs(e1["E"] - e0["E"]) <= 1e-2 * abs(e0["E"])
+    assert abs(e1["M"] + e1["M_out"] - M0) <= 1e-8 * M0
+    assert e1["M_out"] <= 2.5e-4 * M0
+    assert np.abs(enclosed_mass() - m0).max() <= 1e-2 * M0
+    sim.close()
