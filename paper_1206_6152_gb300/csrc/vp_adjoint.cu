@@ -153,8 +153,11 @@ __device__ T line_adjoint(const T *F, const T *LO, T *LI, int C, int t, int n,
 // generic line-adjoint kernel: blockIdx.y selects the outer index (position
 // axes) or the spatial cell (velocity axes); threads take consecutive lines
 template <typename T>
-__global__ void __launch_bounds__(128) k_sweep_adjoint(AdjArgs<T> A, LineGeom g)
+__global__ void __launch_bounds__(128) k_sweep_adjoint(AdjArgs<T> A, LineGeom g,
+                                                      const int *only_shifted)
 {
+    // after the register kernel: nothing to do unless it skipped a line
+    if (only_shifted && *only_shifted == 0) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int C = blockDim.x;
     const int n = g.n;
@@ -164,7 +167,7 @@ __global__ void __launch_bounds__(128) k_sweep_adjoint(AdjArgs<T> A, LineGeom g)
     __shared__ double red[32];
     const int t = threadIdx.x;
     const long long w = (long long)blockIdx.x * C + t;
-    const bool active = w < g.nlines_inner;
+    bool active = w < g.nlines_inner;
     long long base;
     LineCoef<T> cf;
     if (g.axis < 3) {
@@ -178,6 +181,7 @@ __global__ void __launch_bounds__(128) k_sweep_adjoint(AdjArgs<T> A, LineGeom g)
         base = cell * g.nvc + voff;
         cf = A.coef[cell * 3 + (g.axis - 3)];
     }
+    if (only_shifted && active && (cf.code >> 1) == 0) active = false;
     for (int j = 0; j < n; ++j) {
         F[j * C + t] = active ? A.fin[base + j * g.stride] : T(0);
         LO[j * C + t] = active ? A.lam[base + j * g.stride] : T(0);
@@ -276,6 +280,169 @@ __global__ void k_misfit(const double *__restrict__ rho, const double *__restric
     if (threadIdx.x == 0) out[0] = a.value();
 }
 
+// ---------------------------------------------------------------------------
+// register-line adjoint (line lengths 16/32/48/64, zero whole-cell shift):
+// the line of f, the output cotangent and the input cotangent live in
+// registers; the arms are evaluated with the same strict comparisons as
+// line_adjoint.  A line with a whole-cell shift is left untouched and
+// flagged for the generic kernel.
+// ---------------------------------------------------------------------------
+template <typename T, int N, bool PERIODIC, bool NEG>
+__device__ __forceinline__ T adjoint_regs(const T (&f)[N], const T (&lo)[N], T (&li)[N],
+                                          const LineCoef<T> &cf)
+{
+#define M(j) (NEG ? N - 1 - (j) : (j))
+    const T c0 = cf.c0, c1 = cf.c1, c2 = cf.c2;
+    const T beta = c0;
+    const T dc1 = (T(2) - T(6) * beta + T(3) * beta * beta) / T(6);
+    const T dc2 = (T(1) - T(3) * beta * beta) / T(6);
+    T finf = T(0);
+    int arg = 0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const T v = f[M(j)];
+        if (v > finf) { finf = v; arg = j; }
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) li[j] = lo[j];
+    T lfinf = T(0), dbeta = T(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const T lnext = (j + 1 < N) ? lo[M(j + 1)] : (PERIODIC ? lo[M(0)] : T(0));
+        const T mu = lnext - lo[M(j)];
+        const T fm = (j > 0) ? f[M(j - 1)] : (PERIODIC ? f[M(N - 1)] : T(0));
+        const T f0 = f[M(j)];
+        const T fp = (j + 1 < N) ? f[M(j + 1)] : (PERIODIC ? f[M(0)] : T(0));
+        const T two_f0 = T(2) * f0, two_gap = T(2) * (finf - f0);
+        const T dp = fp - f0, dm = f0 - fm;
+        const bool pu = dp > T(0) && two_f0 < dp;
+        const bool pl = !pu && dp < T(0) && -two_gap > dp;
+        const bool mup = dm > T(0) && two_gap < dm;
+        const bool mlo = !mup && dm < T(0) && -two_f0 > dm;
+        const T ep = pu ? two_f0 : (pl ? -two_gap : dp);
+        const T em = mup ? two_gap : (mlo ? -two_f0 : dm);
+        const T a = c1 * mu, b = c2 * mu;
+        T l0 = c0 * mu;
+        l0 += (pu || pl) ? T(2) * a : -a;
+        l0 += (mup || mlo) ? -T(2) * b : b;
+        lfinf += (pl ? -T(2) * a : T(0)) + (mup ? T(2) * b : T(0));
+        li[M(j)] += l0;
+        if (!(pu || pl)) {
+            if (j + 1 < N) li[M(j + 1)] += a;
+            else if (PERIODIC) li[M(0)] += a;
+        }
+        if (!(mup || mlo)) {
+            if (j > 0) li[M(j - 1)] -= b;
+            else if (PERIODIC) li[M(N - 1)] -= b;
+        }
+        dbeta += mu * (f0 + dc1 * ep + dc2 * em);
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+        if (j == arg) li[M(j)] += lfinf;
+#undef M
+    return NEG ? -dbeta : dbeta;
+}
+
+template <typename T, int N, bool PERIODIC, bool ROWS>
+__global__ void __launch_bounds__(128) k_adjoint_fast(AdjArgs<T> A, LineGeom g, int *skipped)
+{
+    __shared__ double red[32];
+    const int t = threadIdx.x;
+    const long long w = (long long)blockIdx.x * blockDim.x + t;
+    bool active = w < g.nlines_inner;
+    long long base = 0;
+    LineCoef<T> cf;
+    if (g.axis < 3) {
+        const int o = blockIdx.y;
+        const long long cell0 = (long long)(o / g.od) * g.m1 + (long long)(o % g.od) * g.m2;
+        base = cell0 * g.nvc + w;
+        if (active) cf = A.coef[(int)((w / A.va_stride) % A.va_n)];
+    } else {
+        const long long cell = blockIdx.y;
+        const long long voff = (w / g.wdiv) * g.wmul_hi + (w % g.wdiv) * g.wmul_lo;
+        base = cell * g.nvc + voff;
+        cf = A.coef[cell * 3 + (g.axis - 3)];
+    }
+    if (active && (cf.code >> 1) != 0) {
+        atomicExch(skipped, 1);
+        active = false;
+    }
+    double da = 0.0;
+    if (active) {
+        T f[N], lo[N], li[N];
+        if constexpr (ROWS && sizeof(T) == 4) {
+#pragma unroll
+            for (int j = 0; j < N; j += 4) {
+                const float4 a = *reinterpret_cast<const float4 *>(A.fin + base + j);
+                const float4 b = *reinterpret_cast<const float4 *>(A.lam + base + j);
+                f[j] = a.x; f[j + 1] = a.y; f[j + 2] = a.z; f[j + 3] = a.w;
+                lo[j] = b.x; lo[j + 1] = b.y; lo[j + 2] = b.z; lo[j + 3] = b.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                f[j] = A.fin[base + j * g.stride];
+                lo[j] = A.lam[base + j * g.stride];
+            }
+        }
+        const T d = (cf.code & 1) ? adjoint_regs<T, N, PERIODIC, true>(f, lo, li, cf)
+                                  : adjoint_regs<T, N, PERIODIC, false>(f, lo, li, cf);
+        da = (double)d;
+        if constexpr (ROWS && sizeof(T) == 4) {
+#pragma unroll
+            for (int j = 0; j < N; j += 4)
+                *reinterpret_cast<float4 *>(A.lam + base + j) =
+                    make_float4(li[j], li[j + 1], li[j + 2], li[j + 3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < N; ++j) A.lam[base + j * g.stride] = li[j];
+        }
+    }
+    if (A.lam_g) {
+        da = block_sum(da, red);
+        if (t == 0 && da != 0.0) atomicAdd(A.lam_g + blockIdx.y, da * A.dalpha_scale);
+    }
+}
+
+int vp_adjoint_fast_ok(const vp_ctx *c, int axis)
+{
+    const int n = axis < 3 ? c->n[axis] : c->nv[axis - 3];
+    if (c->isdouble) return n == 16;
+    return n == 16 || n == 32 || n == 48 || n == 64;
+}
+
+template <typename T, int N>
+cudaError_t adjoint_fast_n(vp_ctx *c, const AdjArgs<T> &A, const LineGeom &g, dim3 grid)
+{
+    const bool rows = g.stride == 1 && sizeof(T) == 4 && (c->nvc % 4) == 0;
+    if (A.periodic) {
+        if (rows) k_adjoint_fast<T, N, true, true><<<grid, 128, 0, c->stream>>>(A, g, c->adj_flag);
+        else k_adjoint_fast<T, N, true, false><<<grid, 128, 0, c->stream>>>(A, g, c->adj_flag);
+    } else {
+        if (rows) k_adjoint_fast<T, N, false, true><<<grid, 128, 0, c->stream>>>(A, g, c->adj_flag);
+        else k_adjoint_fast<T, N, false, false><<<grid, 128, 0, c->stream>>>(A, g, c->adj_flag);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_adjoint_fast(vp_ctx *c, const AdjArgs<T> &A, const LineGeom &g, dim3 grid)
+{
+    cudaError_t e = cudaMemsetAsync(c->adj_flag, 0, sizeof(int), c->stream);
+    if (e != cudaSuccess) return e;
+    if constexpr (sizeof(T) == 8) {
+        return adjoint_fast_n<T, 16>(c, A, g, grid);
+    } else {
+        switch (g.n) {
+        case 16: return adjoint_fast_n<T, 16>(c, A, g, grid);
+        case 32: return adjoint_fast_n<T, 32>(c, A, g, grid);
+        case 48: return adjoint_fast_n<T, 48>(c, A, g, grid);
+        default: return adjoint_fast_n<T, 64>(c, A, g, grid);
+        }
+    }
+}
+
 template <typename T>
 cudaError_t sweep_adjoint_t(vp_ctx *c, const T *fin, T *lam, int axis, const LineCoef<T> *coef,
                             double *lam_g, double dalpha_scale)
@@ -321,7 +488,14 @@ cudaError_t sweep_adjoint_t(vp_ctx *c, const T *fin, T *lam, int axis, const Lin
     cudaError_t e = cudaFuncSetAttribute(k_sweep_adjoint<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_sweep_adjoint<T><<<grid, C, smem, c->stream>>>(A, g);
+    if (vp_adjoint_fast_ok(c, axis)) {
+        e = launch_adjoint_fast<T>(c, A, g, grid);
+        if (e != cudaSuccess) return e;
+        // lines the register kernel skipped (whole-cell shifts), if any
+        k_sweep_adjoint<T><<<grid, C, smem, c->stream>>>(A, g, c->adj_flag);
+        return cudaGetLastError();
+    }
+    k_sweep_adjoint<T><<<grid, C, smem, c->stream>>>(A, g, nullptr);
     return cudaGetLastError();
 }
 
@@ -336,6 +510,10 @@ inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 int ensure_adjoint_scratch(vp_ctx *c)
 {
     if (c->adj_states) return VP_OK;
+    if (c->adj_flag) {
+        cudaFree(c->adj_flag);
+        c->adj_flag = nullptr;
+    }
     const size_t bytes = (size_t)c->ncells * c->esize;
     c->adj_nstates = 9;
     c->adj_states = (void **)calloc(9, sizeof(void *));
@@ -349,7 +527,8 @@ int ensure_adjoint_scratch(vp_ctx *c)
     if (cudaMalloc(&c->adj_f, cs * 3 * c->np) != cudaSuccess ||   // K1 table of the replay
         cudaMalloc((void **)&c->adj_g, sizeof(double) * 3 * c->np) != cudaSuccess ||
         cudaMalloc((void **)&c->adj_lg, sizeof(double) * 3 * c->np) != cudaSuccess ||
-        cudaMalloc((void **)&c->adj_tmp, sizeof(double) * c->nfft) != cudaSuccess) {
+        cudaMalloc((void **)&c->adj_tmp, sizeof(double) * c->nfft) != cudaSuccess ||
+        cudaMalloc((void **)&c->adj_flag, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         return VP_ERR_OOM;
     }
@@ -413,6 +592,10 @@ int vp_sweep_adjoint(vp_ctx *c, int axis, double tau, const void *f_in, void *la
                      double *lambda_g)
 {
     if (!c || !f_in || !lambda || axis < 0 || axis > 5 || !isfinite(tau)) return VP_ERR_ARG;
+    if (!c->adj_flag && cudaMalloc((void **)&c->adj_flag, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return VP_ERR_OOM;
+    }
     double *tau_ptr = &c->sc->pad[3];
     k_set<<<1, 1, 0, c->stream>>>(tau_ptr, tau);
     VP_CUDA_TRY(cudaGetLastError());
@@ -479,23 +662,21 @@ int vp_adjoint_step(vp_ctx *c, const void *f_start, const double *g_start, void 
     void *k1 = c->adj_f;
     VP_CUDA_TRY(launch_coef_kick(c, g_start, tau_ptr, 0.5, k1));
     VP_CUDA_TRY(launch_coef_drift(c, tau_ptr, 1.0, c->coef_drift));
-    // forward replay, keeping every sweep input S[0..8]
+    // forward replay, keeping every sweep input: S[0] = f^n, S[k+1] = sweep k of S[k]
     VP_CUDA_TRY(cudaMemcpyAsync(S[0], f_start, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    const double amax = vp_drift_alpha_bound(c, dt);
     for (int k = 0; k < 8; ++k) {
-        VP_CUDA_TRY(cudaMemcpyAsync(S[k + 1], S[k], bytes, cudaMemcpyDeviceToDevice, c->stream));
         if (k < 3) {
-            VP_CUDA_TRY(launch_kick(c, S[k + 1], k1, nullptr, 1, k));
+            VP_CUDA_TRY(launch_sweep_into(c, S[k], S[k + 1], 3 + k, k1, amax));
         } else if (k < 6) {
-            const int axis = 5 - k;                       // z, y, x
-            VP_CUDA_TRY(launch_drift(c, S[k + 1], axis, c->coef_drift, vp_drift_alpha_bound(c, dt),
-                                     nullptr));
+            VP_CUDA_TRY(launch_sweep_into(c, S[k], S[k + 1], 5 - k, c->coef_drift, amax));
             if (k == 5) {
                 VP_CUDA_TRY(launch_density(c, S[6], c->rho2));
                 VP_CUDA_TRY(launch_field_solve(c, c->rho2, c->adj_g));
                 VP_CUDA_TRY(launch_coef_kick(c, c->adj_g, tau_ptr, 0.5, c->coef_kick2));
             }
         } else {
-            VP_CUDA_TRY(launch_kick(c, S[k + 1], c->coef_kick2, nullptr, 1, k - 6));
+            VP_CUDA_TRY(launch_sweep_into(c, S[k], S[k + 1], 3 + (k - 6), c->coef_kick2, amax));
         }
     }
     // K2 (vz, vy, vx) reversed; its g-cotangent is added to lambda_g^{n+1}

@@ -45,7 +45,7 @@ void free_ctx(vp_ctx *c)
     void *bufs[] = {c->rho, c->phi, c->g, c->cbuf, c->ghat, c->coef_kick1, c->coef_kick2,
                     c->coef_drift, c->vc[0], c->vc[1], c->vc[2], c->red, c->rho2, c->rho_part, c->sc,
                     c->ax[0].tw, c->ax[1].tw, c->ax[2].tw, c->adj_f, c->adj_g, c->adj_lg,
-                    c->adj_tmp};
+                    c->adj_tmp, c->adj_flag};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->adj_states) {

@@ -93,6 +93,7 @@ struct vp_ctx {
     double *adj_g;              // 3 np
     double *adj_lg;             // 3 np
     double *adj_tmp;            // nfft
+    int *adj_flag;              // set when the register adjoint skipped a line
     void **adj_states;          // nine sweep inputs (f's dtype)
     int adj_nstates;
 };
@@ -130,9 +131,17 @@ int vp_kick_fast_ok(const vp_ctx *c);
 int vp_drift_fast_ok(const vp_ctx *c, int axis);
 int vp_rho_fuse_ok(const vp_ctx *c);
 int vp_rho_parts(vp_ctx *c);
+// fo: output array (nullptr: in place)
+// inter0/inter1: optional copies of the cube after sweeps 0 and 1
 cudaError_t launch_kick_fast(vp_ctx *c, void *f, const void *ca, const void *cb, int nsweeps,
-                             int first_axis);
-cudaError_t launch_drift_fast(vp_ctx *c, void *f, int axis, const void *coef, double *rho_part);
+                             int first_axis, void *fo = nullptr, void *inter0 = nullptr,
+                             void *inter1 = nullptr);
+cudaError_t launch_drift_fast(vp_ctx *c, void *f, int axis, const void *coef, double *rho_part,
+                              void *fo = nullptr);
+// one sweep from src into dst (dst != src), used by the adjoint's replay;
+// kick tables [np][3], drift tables [3][maxnv]
+cudaError_t launch_sweep_into(vp_ctx *c, const void *src, void *dst, int axis, const void *coef,
+                              double drift_alpha_bound);
 cudaError_t launch_rho_finish(vp_ctx *c, const double *part, int nparts, double *rho);
 
 int vp_fft_plan_axis(FFTAxis *a, int n);

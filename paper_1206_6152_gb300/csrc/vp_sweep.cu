@@ -491,6 +491,20 @@ cudaError_t launch_kick(vp_ctx *c, void *f, const void *coef_a, const void *coef
                                        (const LineCoef<float> *)coef_b, nsweeps, first_axis);
 }
 
+cudaError_t launch_sweep_into(vp_ctx *c, const void *src, void *dst, int axis, const void *coef,
+                              double drift_alpha_bound)
+{
+    if (axis >= 3 && vp_kick_fast_ok(c))
+        return launch_kick_fast(c, const_cast<void *>(src), coef, nullptr, 1, axis - 3, dst);
+    if (axis < 3 && vp_drift_fast_ok(c, axis) && drift_alpha_bound < 1.0)
+        return launch_drift_fast(c, const_cast<void *>(src), axis, coef, nullptr, dst);
+    cudaError_t e = cudaMemcpyAsync(dst, src, (size_t)c->ncells * c->esize,
+                                    cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return e;
+    if (axis < 3) return launch_drift(c, dst, axis, coef, drift_alpha_bound, nullptr);
+    return launch_kick(c, dst, coef, nullptr, 1, axis - 3);
+}
+
 cudaError_t launch_density(vp_ctx *c, const void *f, double *rho)
 {
     long long grid = (long long)sm_count() * 8;

@@ -205,8 +205,9 @@ __device__ __forceinline__ float sweep_pairs(float2 (&x)[N], const LineCoef<floa
 
 // whole cube through shared memory (a sweep moves by whole cells)
 template <int N>
-__device__ __noinline__ float kick_cube_shifted(float *g, float *cube, const LineCoef<float> *cf,
-                                                int nsweeps, int first_axis)
+__device__ __noinline__ float kick_cube_shifted(const float *g, float *go, float *cube,
+                                                const LineCoef<float> *cf, int nsweeps,
+                                                int first_axis)
 {
     constexpr int P = KickCube<N>::P;
     constexpr int NT = KickCube<N>::NT;
@@ -233,7 +234,7 @@ __device__ __noinline__ float kick_cube_shifted(float *g, float *cube, const Lin
     }
     for (int e = t; e < NC / 4; e += NT) {
         const int r = (4 * e) / N, k = (4 * e) % N;
-        reinterpret_cast<float4 *>(g)[e] = *reinterpret_cast<const float4 *>(cube + r * P + k);
+        reinterpret_cast<float4 *>(go)[e] = *reinterpret_cast<const float4 *>(cube + r * P + k);
     }
     return lost;
 }
@@ -243,7 +244,9 @@ __global__ void __launch_bounds__(KickCube<N>::NT) k_kick_fast(float *__restrict
                                                              const LineCoef<float> *__restrict__ ca,
                                                              const LineCoef<float> *__restrict__ cb,
                                                              int nsweeps, int first_axis, long long np,
-                                                             double *lost_out)
+                                                             double *lost_out, float *__restrict__ fo,
+                                                             float *__restrict__ inter0,
+                                                             float *__restrict__ inter1)
 {
     constexpr int NC = KickCube<N>::NC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -255,6 +258,7 @@ __global__ void __launch_bounds__(KickCube<N>::NT) k_kick_fast(float *__restrict
     int par = 0;
     for (long long cell = blockIdx.x; cell < np; cell += gridDim.x, par ^= 1) {
         float *g = f + cell * (long long)NC;
+        float *go = fo + cell * (long long)NC;          // output cube (== g in place)
         if (t < nsweeps) scf[par][t] = (t < 3 ? ca : cb)[cell * 3 + (first_axis + t) % 3];
         // first sweep: lines straight from global memory, issued before the
         // barrier that publishes the coefficients and retires the previous
@@ -266,7 +270,7 @@ __global__ void __launch_bounds__(KickCube<N>::NT) k_kick_fast(float *__restrict
         bool shifted = false;
         for (int sw = 0; sw < nsweeps; ++sw) shifted |= (scf[par][sw].code >> 1) != 0;
         if (shifted) {
-            lost += kick_cube_shifted<N>(g, cube, scf[par], nsweeps, first_axis);
+            lost += kick_cube_shifted<N>(g, go, cube, scf[par], nsweeps, first_axis);
             continue;
         }
         for (int sw = 0; sw < nsweeps; ++sw) {
@@ -279,11 +283,18 @@ __global__ void __launch_bounds__(KickCube<N>::NT) k_kick_fast(float *__restrict
             }
             lost += sweep_pairs<N>(x, cf);
             if (va < 2) {
-                if (last) store_pairs<N, true>(g, va, t, x);
+                if (last) store_pairs<N, true>(go, va, t, x);
                 else store_pairs<N, false>(cube, va, t, x);
             } else {
-                if (last) store_rows<N, true>(g, t, x);
+                if (last) store_rows<N, true>(go, t, x);
                 else store_rows<N, false>(cube, t, x);
+            }
+            // intermediate states for the adjoint's replay
+            float *ist = sw == 0 ? inter0 : (sw == 1 ? inter1 : nullptr);
+            if (!last && ist) {
+                float *gi = ist + cell * (long long)NC;
+                if (va < 2) store_pairs<N, true>(gi, va, t, x);
+                else store_rows<N, true>(gi, t, x);
             }
             if (!last) {
                 const int vb = (first_axis + sw + 1) % 3;
@@ -340,10 +351,10 @@ __device__ __forceinline__ long long unit_to_v(long long L, const DriftGeom &g, 
 }
 
 template <typename T, int N, bool PERIODIC, bool RHO>
-__global__ void __launch_bounds__(128) k_drift_fast(T *__restrict__ f,
+__global__ void __launch_bounds__(128) k_drift_fast(const T *__restrict__ f,
                                                    const LineCoef<T> *__restrict__ coef,
                                                    DriftGeom g, double *__restrict__ rho_part,
-                                                   double *lost_out)
+                                                   double *lost_out, T *__restrict__ fo)
 {
     typedef typename DriftVec<T>::V V;
     constexpr int W = DriftVec<T>::W;
@@ -351,7 +362,8 @@ __global__ void __launch_bounds__(128) k_drift_fast(T *__restrict__ f,
     const int o = blockIdx.y;
     const long long base_cell = (long long)(o / g.od) * g.m1 + (long long)(o % g.od) * g.m2;
     const long long gstride = g.cell_stride * g.nvc;
-    T *fb = f + base_cell * g.nvc;
+    const T *fb = f + base_cell * g.nvc;
+    T *ob = fo + base_cell * g.nvc;
     const long long u0 = (long long)blockIdx.x * g.per_part;
     long long u1 = u0 + g.per_part;
     if (u1 > g.nunits) u1 = g.nunits;
@@ -360,7 +372,8 @@ __global__ void __launch_bounds__(128) k_drift_fast(T *__restrict__ f,
     for (long long L = u0 + threadIdx.x; L < u1; L += blockDim.x) {
         const long long v = unit_to_v(L, g, W);
         V x[N];
-        T *p = fb + v;
+        const T *p = fb + v;
+        T *q = ob + v;
 #pragma unroll
         for (int j = 0; j < N; ++j) x[j] = *reinterpret_cast<const V *>(p + j * gstride);
         if constexpr (W == 2) {
@@ -392,7 +405,7 @@ __global__ void __launch_bounds__(128) k_drift_fast(T *__restrict__ f,
             lost += update_line<V, N, PERIODIC>(x, w, ca.code & 1);
         }
 #pragma unroll
-        for (int j = 0; j < N; ++j) *reinterpret_cast<V *>(p + j * gstride) = x[j];
+        for (int j = 0; j < N; ++j) *reinterpret_cast<V *>(q + j * gstride) = x[j];
         if constexpr (RHO) {
 #pragma unroll
             for (int j = 0; j < N; ++j) {
@@ -432,7 +445,7 @@ __global__ void k_rho_finish(const double *__restrict__ part, int nparts, long l
 
 template <int N>
 cudaError_t kick_fast_n(vp_ctx *c, float *f, const LineCoef<float> *ca, const LineCoef<float> *cb,
-                        int nsweeps, int first_axis)
+                        int nsweeps, int first_axis, float *fo, float *inter0, float *inter1)
 {
     constexpr int P = KickCube<N>::P;
     const size_t smem = (size_t)N * N * P * sizeof(float);
@@ -447,13 +460,13 @@ cudaError_t kick_fast_n(vp_ctx *c, float *f, const LineCoef<float> *ca, const Li
     long long grid = (long long)per_sm * vp_sm_count();
     if (grid > c->np) grid = c->np;
     kern<<<(unsigned)grid, threads, smem, c->stream>>>(f, ca, cb, nsweeps, first_axis, c->np,
-                                                       &c->sc->lost);
+                                                       &c->sc->lost, fo ? fo : f, inter0, inter1);
     return cudaGetLastError();
 }
 
 template <typename T, int N>
 cudaError_t drift_fast_n(vp_ctx *c, T *f, int axis, const LineCoef<T> *coef, double *rho_part,
-                         int nparts)
+                         int nparts, T *fo)
 {
     DriftGeom g;
     if (axis == 0) {
@@ -494,17 +507,17 @@ cudaError_t drift_fast_n(vp_ctx *c, T *f, int axis, const LineCoef<T> *coef, dou
     if (c->periodic_space) {
         if constexpr (RHO_OK)
             if (rho) {
-                k_drift_fast<T, N, true, true><<<grid, 128, 0, c->stream>>>(f, coef, g, rho_part, &c->sc->lost);
+                k_drift_fast<T, N, true, true><<<grid, 128, 0, c->stream>>>(f, coef, g, rho_part, &c->sc->lost, fo ? fo : f);
                 return cudaGetLastError();
             }
-        k_drift_fast<T, N, true, false><<<grid, 128, 0, c->stream>>>(f, coef, g, rho_part, &c->sc->lost);
+        k_drift_fast<T, N, true, false><<<grid, 128, 0, c->stream>>>(f, coef, g, rho_part, &c->sc->lost, fo ? fo : f);
     } else {
         if constexpr (RHO_OK)
             if (rho) {
-                k_drift_fast<T, N, false, true><<<grid, 128, 0, c->stream>>>(f, coef, g, rho_part, &c->sc->lost);
+                k_drift_fast<T, N, false, true><<<grid, 128, 0, c->stream>>>(f, coef, g, rho_part, &c->sc->lost, fo ? fo : f);
                 return cudaGetLastError();
             }
-        k_drift_fast<T, N, false, false><<<grid, 128, 0, c->stream>>>(f, coef, g, rho_part, &c->sc->lost);
+        k_drift_fast<T, N, false, false><<<grid, 128, 0, c->stream>>>(f, coef, g, rho_part, &c->sc->lost, fo ? fo : f);
     }
     return cudaGetLastError();
 }
@@ -546,29 +559,32 @@ int vp_rho_fuse_ok(const vp_ctx *c)
 }
 
 cudaError_t launch_kick_fast(vp_ctx *c, void *f, const void *ca, const void *cb, int nsweeps,
-                             int first_axis)
+                             int first_axis, void *fo, void *inter0, void *inter1)
 {
     if (c->nv[0] == 32)
         return kick_fast_n<32>(c, (float *)f, (const LineCoef<float> *)ca,
-                               (const LineCoef<float> *)cb, nsweeps, first_axis);
+                               (const LineCoef<float> *)cb, nsweeps, first_axis, (float *)fo,
+                               (float *)inter0, (float *)inter1);
     return kick_fast_n<16>(c, (float *)f, (const LineCoef<float> *)ca, (const LineCoef<float> *)cb,
-                           nsweeps, first_axis);
+                           nsweeps, first_axis, (float *)fo, (float *)inter0, (float *)inter1);
 }
 
-cudaError_t launch_drift_fast(vp_ctx *c, void *f, int axis, const void *coef, double *rho_part)
+cudaError_t launch_drift_fast(vp_ctx *c, void *f, int axis, const void *coef, double *rho_part,
+                              void *fo)
 {
     const int n = c->n[axis];
     const int np = rho_part ? vp_rho_parts(c) : 0;
     if (c->isdouble) {
         const LineCoef<double> *cf = (const LineCoef<double> *)coef + (size_t)axis * c->maxnv;
-        return drift_fast_n<double, 16>(c, (double *)f, axis, cf, rho_part, np);
+        return drift_fast_n<double, 16>(c, (double *)f, axis, cf, rho_part, np, (double *)fo);
     }
     const LineCoef<float> *cf = (const LineCoef<float> *)coef + (size_t)axis * c->maxnv;
+    float *o = (float *)fo;
     switch (n) {
-    case 16: return drift_fast_n<float, 16>(c, (float *)f, axis, cf, rho_part, np);
-    case 32: return drift_fast_n<float, 32>(c, (float *)f, axis, cf, rho_part, np);
-    case 48: return drift_fast_n<float, 48>(c, (float *)f, axis, cf, nullptr, 0);
-    default: return drift_fast_n<float, 64>(c, (float *)f, axis, cf, nullptr, 0);
+    case 16: return drift_fast_n<float, 16>(c, (float *)f, axis, cf, rho_part, np, o);
+    case 32: return drift_fast_n<float, 32>(c, (float *)f, axis, cf, rho_part, np, o);
+    case 48: return drift_fast_n<float, 48>(c, (float *)f, axis, cf, nullptr, 0, o);
+    default: return drift_fast_n<float, 64>(c, (float *)f, axis, cf, nullptr, 0, o);
     }
 }
 

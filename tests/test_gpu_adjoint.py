@@ -61,6 +61,43 @@ def test_sweep_adjoint_matches_oracle(space_bc):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("dtype,shape", [("f64", dict(n=(16, 16, 16), nv=(16, 16, 16))),
+                                         ("f32", dict(n=(16, 32, 16), nv=(16, 16, 32)))])
+def test_register_adjoint_sweeps_match_oracle(dtype, shape):
+    """Line lengths served by the register-line adjoint kernel."""
+    w = I.small_maxwell(dtype=dtype, amp=0.3, **shape)
+    w = w.replace(box_lo=(-0.5,) * 3, box_hi=(0.5,) * 3)
+    grid = O.Grid.of(w)
+    rng = np.random.default_rng(9)
+    npdt = np.float32 if dtype == "f32" else np.float64
+    f0 = (I.initial_condition(w, np.float64) * (1 + 0.5 * rng.random(w.shape))).astype(npdt)
+    acc = rng.normal(size=(3,) + w.n) * 3
+    sim, f = gpu_sim(w, f0)
+    sim.set_accel(torch.from_numpy(acc))
+    for axis in range(6):
+        for tau in (0.011, -0.017):
+            lam0 = rng.normal(size=w.shape).astype(npdt)
+            lam = torch.from_numpy(lam0).to(DEV)
+            lg = torch.zeros((3,) + w.n, dtype=torch.float64, device=DEV)
+            sim.sweep_adjoint(axis, tau, torch.from_numpy(f0).to(DEV), lam, lg)
+            ref = lam0.astype(np.float64)
+            ds = np.zeros(int(np.prod(w.n)))
+            f64 = f0.astype(np.float64)
+            if axis < 3:
+                O.sweep_adjoint(f64, ref, axis, grid.vc(axis), tau, grid.dx[axis], True, None)
+            else:
+                O.sweep_adjoint(f64, ref, axis, acc[axis - 3], tau, grid.dv[axis - 3], False, ds)
+            got = lam.cpu().numpy().astype(np.float64)
+            rel = np.abs(got - ref).sum() / np.abs(ref).sum()
+            assert rel <= (1e-13 if dtype == "f64" else 1e-6), (axis, tau, rel)
+            if axis >= 3:
+                gg = lg.cpu().numpy()[axis - 3].reshape(-1)
+                relg = np.abs(gg - ds).sum() / np.abs(ds).sum()
+                assert relg <= (1e-12 if dtype == "f64" else 1e-5), (axis, tau, relg)
+    sim.close()
+
+
+@pytest.mark.gpu
 @pytest.mark.parametrize("bc", ["periodic", "isolated"])
 def test_adjoint_step_matches_oracle(bc):
     w = I.small_maxwell(n=(6, 5, 4), nv=(8, 7, 6), dtype="f64", amp=0.2, G=20.0)
