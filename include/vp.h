@@ -139,6 +139,8 @@ int vp_step_host(vp_ctx *ctx, const void *f_host_in, void *f_host_out, int nstep
  * the elapsed milliseconds into ms_out[VP_PROFILE_SLOTS] (host):
  *   [0] fused kick pass (6 velocity sweeps)   [1] drift z
  *   [2] drift y                                [3] drift x
+ * (where the z and y drifts run as one fused pass, [1] holds that pass
+ * and [2] brackets no kernel),
  *   [4] density reduction                      [5] Poisson + force
  *   [6] dt, shift tables, time                 [7] whole step
  * The first and last half kicks around the timed body run untimed, so f

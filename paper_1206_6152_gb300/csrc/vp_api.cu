@@ -209,8 +209,12 @@ int enqueue_prologue(vp_ctx *c)
 int enqueue_drift_density(vp_ctx *c)
 {
     const double amax = step_alpha_bound(c);
-    VP_CUDA_TRY(launch_drift(c, c->f, 2, c->coef_drift, amax, nullptr));
-    VP_CUDA_TRY(launch_drift(c, c->f, 1, c->coef_drift, amax, nullptr));
+    if (amax < 1.0 && vp_drift_yz_ok(c)) {
+        VP_CUDA_TRY(launch_drift_yz(c, c->f, c->coef_drift, c->f));
+    } else {
+        VP_CUDA_TRY(launch_drift(c, c->f, 2, c->coef_drift, amax, nullptr));
+        VP_CUDA_TRY(launch_drift(c, c->f, 1, c->coef_drift, amax, nullptr));
+    }
     if (c->rho_part && vp_rho_fuse_ok(c) && amax < 1.0) {
         VP_CUDA_TRY(launch_drift(c, c->f, 0, c->coef_drift, amax, c->rho_part));
         VP_CUDA_TRY(launch_rho_finish(c, c->rho_part, c->rho_nparts, c->rho));
@@ -590,9 +594,14 @@ int vp_profile_step(vp_ctx *c, double *ms_out)
         const double amax = step_alpha_bound(c);
         const bool fuse = c->rho_part && vp_rho_fuse_ok(c) && amax < 1.0;
         PROF(rec(0));
-        PROF(launch_drift(c, c->f, 2, c->coef_drift, amax, nullptr));
-        PROF(rec(1));
-        PROF(launch_drift(c, c->f, 1, c->coef_drift, amax, nullptr));
+        if (amax < 1.0 && vp_drift_yz_ok(c)) {
+            PROF(launch_drift_yz(c, c->f, c->coef_drift, c->f));
+            PROF(rec(1));
+        } else {
+            PROF(launch_drift(c, c->f, 2, c->coef_drift, amax, nullptr));
+            PROF(rec(1));
+            PROF(launch_drift(c, c->f, 1, c->coef_drift, amax, nullptr));
+        }
         PROF(rec(2));
         PROF(launch_drift(c, c->f, 0, c->coef_drift, amax, fuse ? c->rho_part : nullptr));
         PROF(rec(3));

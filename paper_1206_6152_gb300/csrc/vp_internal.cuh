@@ -133,6 +133,9 @@ int vp_rho_fuse_ok(const vp_ctx *c);
 int vp_rho_parts(vp_ctx *c);
 // fo: output array (nullptr: in place)
 // inter0/inter1: optional copies of the cube after sweeps 0 and 1
+// fused z then y drift of the whole grid (in place when fo == f)
+int vp_drift_yz_ok(const vp_ctx *c);
+cudaError_t launch_drift_yz(vp_ctx *c, const void *f, const void *coef, void *fo);
 cudaError_t launch_kick_fast(vp_ctx *c, void *f, const void *ca, const void *cb, int nsweeps,
                              int first_axis, void *fo = nullptr, void *inter0 = nullptr,
                              void *inter1 = nullptr);

@@ -1,16 +1,17 @@
 // vp_line.cuh -- the PFC update of one line held in registers (Sec. 2.1 of
 // Yoshikawa, Yoshida & Umemura 2013), for lines of compile-time length N.
 //
-// Slope corrector in saturating-multiply form.  With a = 2 f_j,
-// F = 2 f_inf (f_inf the line maximum) and the one-sided differences
-// d+ = f_{j+1} - f_j, d- = f_j - f_{j-1}, the corrected differences of
-// Filbet, Sonnendruecker & Bertrand (2001) are
+// Slope corrector in saturating form.  With a = 2 f_j, F = 2 f_inf (f_inf
+// the line maximum) and the one-sided differences d+ = f_{j+1} - f_j,
+// d- = f_j - f_{j-1}, the corrected differences of Filbet, Sonnendruecker &
+// Bertrand (2001) are
 //   E+ = clamp(d+, -(F - a), a) = a - F sat((3 f_j - f_{j+1}) / F)
 //   E- = clamp(d-, -a, F - a)   = -a + F sat((3 f_j - f_{j-1}) / F)
-// where sat(x) = min(max(x, 0), 1) is the free saturation of a multiply.
+// where sat(x) = min(max(x, 0), 1) is the free saturation of an FMA.  With
+// the scaled values h_j = -f_j / F and r3 = 3 / F the two arguments are
+// single FMAs: s1 = sat(r3 f_j + h_{j+1}), s2 = sat(r3 f_j + h_{j-1}).
 // The partial flux phi_j = c0 f_j + c1 E+ + c2 E- (u > 0) then becomes
-//   phi_j = K0 f_j + A1 s1 + A2 s2,   s1 = sat((3 f_j - f_{j+1}) / F),
-//                                     s2 = sat((3 f_j - f_{j-1}) / F),
+//   phi_j = K0 f_j + A1 s1 + A2 s2,
 //   K0 = c0 + 2 (c1 - c2),  A1 = -c1 F,  A2 = c2 F.
 // For u < 0 the mirrored line gives phi_j = c0 f_j - c2 E+ - c1 E- with the
 // same s1, s2: K0 is unchanged, A1 = c2 F, A2 = -c1 F, and the update takes
@@ -28,15 +29,16 @@ namespace vpline {
 // small vector abstraction: float2 (two lines packed, f32x2 instructions) or
 // a scalar float/double (one line)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float mulsat(float a, float b)
+// sat(a b + c) with one rounding
+__device__ __forceinline__ float fmasat(float a, float b, float c)
 {
     float r;
-    asm("mul.rn.sat.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    asm("fma.rn.ftz.sat.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
     return r;
 }
-__device__ __forceinline__ double mulsat(double a, double b)
+__device__ __forceinline__ double fmasat(double a, double b, double c)
 {
-    return fmin(fmax(a * b, 0.0), 1.0);       // NaN -> 0, as the f32 .sat form
+    return fmin(fmax(::fma(a, b, c), 0.0), 1.0);   // NaN -> 0, as the f32 .sat form
 }
 __device__ __forceinline__ float max3(float a, float b, float c)
 {
@@ -62,9 +64,9 @@ struct VOps<float2> {
     {
         return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
     }
-    __device__ __forceinline__ static float2 msat(float2 a, float2 b)
+    __device__ __forceinline__ static float2 fsat(float2 a, float2 b, float2 c)
     {
-        return make_float2(mulsat(a.x, b.x), mulsat(a.y, b.y));
+        return make_float2(fmasat(a.x, b.x, c.x), fmasat(a.y, b.y, c.y));
     }
     __device__ __forceinline__ static float2 vmin(float2 a, float2 b)
     {
@@ -82,7 +84,7 @@ struct VOps<float> {
     __device__ __forceinline__ static float mul(float a, float b) { return a * b; }
     __device__ __forceinline__ static float add(float a, float b) { return a + b; }
     __device__ __forceinline__ static float sub(float a, float b) { return a - b; }
-    __device__ __forceinline__ static float msat(float a, float b) { return mulsat(a, b); }
+    __device__ __forceinline__ static float fsat(float a, float b, float c) { return fmasat(a, b, c); }
     __device__ __forceinline__ static float vmin(float a, float b) { return fminf(a, b); }
     __device__ __forceinline__ static float zero() { return 0.f; }
 };
@@ -96,7 +98,7 @@ struct VOps<double> {
     __device__ __forceinline__ static double mul(double a, double b) { return a * b; }
     __device__ __forceinline__ static double add(double a, double b) { return a + b; }
     __device__ __forceinline__ static double sub(double a, double b) { return a - b; }
-    __device__ __forceinline__ static double msat(double a, double b) { return mulsat(a, b); }
+    __device__ __forceinline__ static double fsat(double a, double b, double c) { return fmasat(a, b, c); }
     __device__ __forceinline__ static double vmin(double a, double b) { return fmin(a, b); }
     __device__ __forceinline__ static double zero() { return 0.0; }
 };
@@ -170,16 +172,14 @@ __device__ __forceinline__ void weights1(S c0, S c1, S c2, int neg, S finf, S &K
     ninvF = F > S(0) ? -recip(F) : S(0);
 }
 
-// phi of one cell from its left, own and right values
+// phi of one cell from its own value and the scaled values h = -f / F of its
+// left and right neighbours (r3 = 3 / F)
 template <typename V>
-__device__ __forceinline__ V flux(V fm, V f0, V fp, const LineW<V> &w)
+__device__ __forceinline__ V flux(V f0, V hm, V hp, const LineW<V> &w, V r3)
 {
     typedef VOps<V> O;
-    const V m3 = O::splat(typename O::S(-3));
-    const V u1 = O::fma(f0, m3, fp);          // f_{j+1} - 3 f_j
-    const V u2 = O::fma(f0, m3, fm);          // f_{j-1} - 3 f_j
-    const V s1 = O::msat(u1, w.ninvF);        // sat((3 f_j - f_{j+1}) / F)
-    const V s2 = O::msat(u2, w.ninvF);
+    const V s1 = O::fsat(f0, r3, hp);         // sat((3 f_j - f_{j+1}) / F)
+    const V s2 = O::fsat(f0, r3, hm);         // sat((3 f_j - f_{j-1}) / F)
     V ph = O::mul(w.K0, f0);
     ph = O::fma(w.A1, s1, ph);
     ph = O::fma(w.A2, s2, ph);
@@ -187,51 +187,58 @@ __device__ __forceinline__ V flux(V fm, V f0, V fp, const LineW<V> &w)
 }
 
 // In-place PFC update of the line x (zero shift, |alpha| < 1).  Returns the
-// amount that left through the outflow end (0 for periodic lines).
+// amount that left through the outflow end (0 for periodic lines).  Every
+// value is read before it is overwritten: the update is a stencil of the old
+// line, and each cell's scaled value h is formed once, as it first becomes a
+// right (u > 0) or left (u < 0) neighbour.
 template <typename V, int N, bool PERIODIC>
 __device__ __forceinline__ V update_line(V (&x)[N], const LineW<V> &w, bool neg)
 {
     typedef VOps<V> O;
+    const V z = O::zero();
+    const V r3 = O::mul(w.ninvF, O::splat(typename O::S(-3)));
     if (!neg) {
-        V fm, phprev;
-        const V x0 = x[0];
+        V hm = z, phprev = z;
+        V hc = O::mul(x[0], w.ninvF);
+        const V h0 = hc;
         if (PERIODIC) {
-            fm = x[N - 1];
-            phprev = flux(N >= 2 ? x[N - 2] : x[0], x[N - 1], x[0], w);
-        } else {
-            fm = O::zero();
-            phprev = O::zero();
+            const V hl = O::mul(x[N - 1], w.ninvF);
+            const V hl2 = N >= 2 ? O::mul(x[N >= 2 ? N - 2 : 0], w.ninvF) : hl;
+            phprev = flux(x[N - 1], hl2, h0, w, r3);
+            hm = hl;
         }
 #pragma unroll
         for (int i = 0; i < N; ++i) {
             const V fc = x[i];
-            const V fp = (i + 1 < N) ? x[i + 1] : (PERIODIC ? x0 : O::zero());
-            const V ph = flux(fm, fc, fp, w);
+            const V hp = (i + 1 < N) ? O::mul(x[i + 1 < N ? i + 1 : 0], w.ninvF) : (PERIODIC ? h0 : z);
+            const V ph = flux(fc, hm, hp, w, r3);
             x[i] = O::add(O::sub(fc, ph), phprev);
             phprev = ph;
-            fm = fc;
+            hm = hc;
+            hc = hp;
         }
-        return PERIODIC ? O::zero() : phprev;
+        return PERIODIC ? z : phprev;
     } else {
-        V fp, phnext;
-        const V xl = x[N - 1];
+        V hp = z, phnext = z;
+        V hc = O::mul(x[N - 1], w.ninvF);
+        const V hl = hc;
         if (PERIODIC) {
-            fp = x[0];
-            phnext = flux(x[N - 1], x[0], N >= 2 ? x[1] : x[0], w);
-        } else {
-            fp = O::zero();
-            phnext = O::zero();
+            const V h0 = O::mul(x[0], w.ninvF);
+            const V h1 = N >= 2 ? O::mul(x[N >= 2 ? 1 : 0], w.ninvF) : h0;
+            phnext = flux(x[0], hl, h1, w, r3);
+            hp = h0;
         }
 #pragma unroll
         for (int i = N - 1; i >= 0; --i) {
             const V fc = x[i];
-            const V fm = (i >= 1) ? x[i - 1] : (PERIODIC ? xl : O::zero());
-            const V ph = flux(fm, fc, fp, w);
+            const V hm = (i >= 1) ? O::mul(x[i >= 1 ? i - 1 : 0], w.ninvF) : (PERIODIC ? hl : z);
+            const V ph = flux(fc, hm, hp, w, r3);
             x[i] = O::add(O::sub(fc, ph), phnext);
             phnext = ph;
-            fp = fc;
+            hp = hc;
+            hc = hm;
         }
-        return PERIODIC ? O::zero() : phnext;
+        return PERIODIC ? z : phnext;
     }
 }
 

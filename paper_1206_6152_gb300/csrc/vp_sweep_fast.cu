@@ -97,10 +97,13 @@ __device__ __forceinline__ LineW<S> weights_one(const LineCoef<S> &cf, S finf)
 // Line ownership: for sweeps along vx and vy each thread owns the two lines
 // at vz = k, k + 1 of one (vy resp. vx) index; for vz it owns two contiguous
 // rows.  The first sweep of a cube reads its lines straight from global
-// memory into registers and the last one writes them straight back, so the
-// cube crosses shared memory only between sweeps.  The next cube's loads are
-// issued before the barrier that protects the buffer, so they overlap the
-// end of the previous cube.
+// memory into registers.  A last sweep along vx or vy writes its lines
+// straight back (a warp store covers two 128-byte rows); a last sweep along
+// vz first writes its rows to shared memory, after which each warp copies
+// the 64 rows it owns out with 16-byte stores that cover 512 contiguous
+// bytes.  The next cube's loads are issued before the barrier that protects
+// the buffer, so they overlap the end of the previous cube, and one bulk L2
+// prefetch per cube brings the cube after next into L2.
 // ---------------------------------------------------------------------------
 template <int N>
 struct KickCube {
@@ -191,6 +194,27 @@ __device__ __forceinline__ void store_rows(float *dst, int t, const float2 (&x)[
         *reinterpret_cast<float4 *>(ra + j) = make_float4(x[j].x, x[j + 1].x, x[j + 2].x, x[j + 3].x);
         *reinterpret_cast<float4 *>(rb + j) = make_float4(x[j].y, x[j + 1].y, x[j + 2].y, x[j + 3].y);
     }
+}
+
+// rows [64 w, 64 w + 64) of the cube belong to warp w in the vz sweep (for
+// N = 16 and N = 32): copy them from shared to global memory, coalesced
+template <int N>
+__device__ __forceinline__ void copy_out_rows(float *go, const float *cube, int warp, int lane)
+{
+    constexpr int Q = N / 4;                    // 16-byte chunks per row
+#pragma unroll 4
+    for (int e = lane; e < 64 * Q; e += 32) {
+        const int r = 64 * warp + e / Q, c = 4 * (e % Q);
+        *reinterpret_cast<float4 *>(go + r * N + c) =
+            *reinterpret_cast<const float4 *>(cube + r * KickCube<N>::P + c);
+    }
+}
+
+// asynchronous prefetch of [p, p + bytes) into L2 (16-byte aligned, bytes a
+// multiple of 16)
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 // one sweep of the owned lines held in registers
@@ -286,8 +310,11 @@ __global__ void __launch_bounds__(KickCube<N>::NT) k_kick_fast(float *__restrict
                 if (last) store_pairs<N, true>(go, va, t, x);
                 else store_pairs<N, false>(cube, va, t, x);
             } else {
-                if (last) store_rows<N, true>(go, t, x);
-                else store_rows<N, false>(cube, t, x);
+                store_rows<N, false>(cube, t, x);
+                if (last) {
+                    __syncwarp();
+                    copy_out_rows<N>(go, cube, t >> 5, t & 31);
+                }
             }
             // intermediate states for the adjoint's replay
             float *ist = sw == 0 ? inter0 : (sw == 1 ? inter1 : nullptr);
@@ -302,6 +329,73 @@ __global__ void __launch_bounds__(KickCube<N>::NT) k_kick_fast(float *__restrict
                 else __syncthreads();
             }
         }
+    }
+    Acc<double> a;
+    a.add((double)lost);
+    a = block_merge(a, red);
+    if (t == 0 && a.value() != 0.0) atomicAdd(lost_out, a.value());
+}
+
+// The fused kick pass K2^n K1^{n+1}: six sweeps vx vy vz vx vy vz of every
+// cube (coefficient tables ca for the first three, cb for the last three),
+// in place or into fo.
+template <int N>
+__global__ void __launch_bounds__(KickCube<N>::NT) k_kick6(float *__restrict__ f,
+                                                         const LineCoef<float> *__restrict__ ca,
+                                                         const LineCoef<float> *__restrict__ cb,
+                                                         long long np, double *lost_out,
+                                                         float *__restrict__ fo)
+{
+    constexpr int NC = KickCube<N>::NC;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *cube = reinterpret_cast<float *>(smem_raw);
+    __shared__ Acc<double> red[32];
+    __shared__ LineCoef<float> scf[2][6];
+    const int t = threadIdx.x;
+    float lost = 0.f;
+    int par = 0;
+    for (long long cell = blockIdx.x; cell < np; cell += gridDim.x, par ^= 1) {
+        float *g = f + cell * (long long)NC;
+        float *go = fo + cell * (long long)NC;
+        if (t < 4) {
+            const long long nx = cell + gridDim.x;
+            if (nx < np) prefetch_l2(f + nx * NC + t * (NC / 4), NC);
+        }
+        if (t < 6) scf[par][t] = (t < 3 ? ca : cb)[cell * 3 + t % 3];
+        float2 x[N];
+        load_pairs<N, true>(g, 0, t, x);
+        __syncthreads();
+        bool shifted = false;
+#pragma unroll
+        for (int sw = 0; sw < 6; ++sw) shifted |= (scf[par][sw].code >> 1) != 0;
+        if (shifted) {
+            lost += kick_cube_shifted<N>(g, go, cube, scf[par], 6, 0);
+            continue;
+        }
+        lost += sweep_pairs<N>(x, scf[par][0]);
+        store_pairs<N, false>(cube, 0, t, x);
+        __syncthreads();
+        load_pairs<N, false>(cube, 1, t, x);
+        lost += sweep_pairs<N>(x, scf[par][1]);
+        store_pairs<N, false>(cube, 1, t, x);
+        __syncwarp();
+        load_rows<N, false>(cube, t, x);
+        lost += sweep_pairs<N>(x, scf[par][2]);
+        store_rows<N, false>(cube, t, x);
+        __syncthreads();
+        load_pairs<N, false>(cube, 0, t, x);
+        lost += sweep_pairs<N>(x, scf[par][3]);
+        store_pairs<N, false>(cube, 0, t, x);
+        __syncthreads();
+        load_pairs<N, false>(cube, 1, t, x);
+        lost += sweep_pairs<N>(x, scf[par][4]);
+        store_pairs<N, false>(cube, 1, t, x);
+        __syncwarp();
+        load_rows<N, false>(cube, t, x);
+        lost += sweep_pairs<N>(x, scf[par][5]);
+        store_rows<N, false>(cube, t, x);
+        __syncwarp();
+        copy_out_rows<N>(go, cube, t >> 5, t & 31);
     }
     Acc<double> a;
     a.add((double)lost);
@@ -432,6 +526,114 @@ __global__ void __launch_bounds__(128) k_drift_fast(const T *__restrict__ f,
     }
 }
 
+// ---------------------------------------------------------------------------
+// fused z and y drift (FP32, N_y = N_z = N): one CTA per (x, chunk of VC
+// velocity cells).  The z sweep reads its lines (pairs of adjacent velocity
+// cells) straight from global memory and writes them to a shared tile
+// [y][z][VC]; the y sweep reads its lines from the tile and writes them
+// straight back.  f crosses HBM once for both sweeps.  The chunk lies inside
+// one vz row, so every y line of the CTA has the same v_y; the z lines of a
+// pair differ in v_z (two coefficients, two scalar lines where the pair
+// straddles the sign change of v_z).
+// ---------------------------------------------------------------------------
+template <int N>
+struct DriftYZ {
+    static constexpr int VC = 512 / N;                 // velocity cells per CTA
+    static constexpr int NT = N * VC / 2;              // threads: one line pair each
+    static constexpr int YP = N * VC + (VC == 16 ? 16 : 0);   // tile pitch of one y
+};
+
+template <int N, bool PERIODIC>
+__device__ __forceinline__ float drift_pair(float2 (&x)[N], const LineCoef<float> &ca,
+                                            const LineCoef<float> &cb)
+{
+    if ((ca.code & 1) == (cb.code & 1)) {
+        const LineW<float2> w = weights_pair2(ca, cb, line_max(x));
+        const float2 out = update_line<float2, N, PERIODIC>(x, w, ca.code & 1);
+        return out.x + out.y;
+    }
+    float y0[N], y1[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) { y0[j] = x[j].x; y1[j] = x[j].y; }
+    const LineW<float> w0 = weights_one<float>(ca, line_max(y0));
+    const LineW<float> w1 = weights_one<float>(cb, line_max(y1));
+    float lost = update_line<float, N, PERIODIC>(y0, w0, ca.code & 1);
+    lost += update_line<float, N, PERIODIC>(y1, w1, cb.code & 1);
+#pragma unroll
+    for (int j = 0; j < N; ++j) x[j] = make_float2(y0[j], y1[j]);
+    return lost;
+}
+
+template <int N, bool PERIODIC>
+__global__ void __launch_bounds__(DriftYZ<N>::NT) k_drift_yz(const float *__restrict__ f,
+                                                           const LineCoef<float> *__restrict__ cz,
+                                                           const LineCoef<float> *__restrict__ cy,
+                                                           long long nvc, int nvy, int nvz,
+                                                           double *lost_out,
+                                                           float *__restrict__ fo)
+{
+    constexpr int VC = DriftYZ<N>::VC, YP = DriftYZ<N>::YP, H = VC / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *tile = reinterpret_cast<float *>(smem_raw);
+    __shared__ Acc<double> red[32];
+    const int t = threadIdx.x, vp = t % H, r = t / H;    // r: y in the z sweep, z in the y sweep
+    const long long v0 = (long long)blockIdx.x * VC;
+    const long long x0 = (long long)blockIdx.y * N * N;  // first spatial cell of the x plane
+    const long long v = v0 + 2 * vp;
+    float lost = 0.f;
+    float2 x[N];
+    {
+        const float *p = f + (x0 + (long long)r * N) * nvc + v;
+#pragma unroll
+        for (int j = 0; j < N; ++j) x[j] = *reinterpret_cast<const float2 *>(p + j * nvc);
+        const LineCoef<float> ca = cz[(int)(v % nvz)], cb = cz[(int)((v + 1) % nvz)];
+        lost += drift_pair<N, PERIODIC>(x, ca, cb);
+        float *q = tile + r * YP + 2 * vp;
+#pragma unroll
+        for (int j = 0; j < N; ++j) *reinterpret_cast<float2 *>(q + j * VC) = x[j];
+    }
+    __syncthreads();
+    {
+        const float *q = tile + r * VC + 2 * vp;
+#pragma unroll
+        for (int j = 0; j < N; ++j) x[j] = *reinterpret_cast<const float2 *>(q + j * YP);
+        const LineCoef<float> c = cy[(int)((v0 / nvz) % nvy)];
+        lost += drift_pair<N, PERIODIC>(x, c, c);
+        float *p = fo + (x0 + r) * nvc + v;
+#pragma unroll
+        for (int j = 0; j < N; ++j) *reinterpret_cast<float2 *>(p + (long long)j * N * nvc) = x[j];
+    }
+    if (!PERIODIC) {
+        Acc<double> a;
+        a.add((double)lost);
+        a = block_merge(a, red);
+        if (t == 0 && a.value() != 0.0) atomicAdd(lost_out, a.value());
+    }
+}
+
+template <int N>
+cudaError_t drift_yz_n(vp_ctx *c, const float *f, const LineCoef<float> *coef, float *fo)
+{
+    constexpr int NT = DriftYZ<N>::NT;
+    const size_t smem = (size_t)N * DriftYZ<N>::YP * sizeof(float);
+    const dim3 grid((unsigned)(c->nvc / DriftYZ<N>::VC), (unsigned)c->n[0]);
+    const LineCoef<float> *cz = coef + (size_t)2 * c->maxnv, *cy = coef + (size_t)c->maxnv;
+    if (c->periodic_space) {
+        cudaError_t e = cudaFuncSetAttribute(k_drift_yz<N, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_drift_yz<N, true><<<grid, NT, smem, c->stream>>>(f, cz, cy, c->nvc, c->nv[1], c->nv[2],
+                                                           &c->sc->lost, fo);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_drift_yz<N, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_drift_yz<N, false><<<grid, NT, smem, c->stream>>>(f, cz, cy, c->nvc, c->nv[1], c->nv[2],
+                                                            &c->sc->lost, fo);
+    }
+    return cudaGetLastError();
+}
+
 // rho = dvol * sum_parts partial (Neumaier)
 __global__ void k_rho_finish(const double *__restrict__ part, int nparts, long long np, double dvol,
                              double *__restrict__ rho)
@@ -443,24 +645,40 @@ __global__ void k_rho_finish(const double *__restrict__ part, int nparts, long l
     rho[t] = a.value() * dvol;
 }
 
-template <int N>
-cudaError_t kick_fast_n(vp_ctx *c, float *f, const LineCoef<float> *ca, const LineCoef<float> *cb,
-                        int nsweeps, int first_axis, float *fo, float *inter0, float *inter1)
+template <typename K>
+cudaError_t kick_grid(vp_ctx *c, K kern, int threads, size_t smem, long long &grid)
 {
-    constexpr int P = KickCube<N>::P;
-    const size_t smem = (size_t)N * N * P * sizeof(float);
-    auto kern = k_kick_fast<N>;
-    const int threads = KickCube<N>::NT;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    long long grid = (long long)per_sm * vp_sm_count();
+    grid = (long long)per_sm * vp_sm_count();
     if (grid > c->np) grid = c->np;
-    kern<<<(unsigned)grid, threads, smem, c->stream>>>(f, ca, cb, nsweeps, first_axis, c->np,
-                                                       &c->sc->lost, fo ? fo : f, inter0, inter1);
+    return cudaSuccess;
+}
+
+template <int N>
+cudaError_t kick_fast_n(vp_ctx *c, float *f, const LineCoef<float> *ca, const LineCoef<float> *cb,
+                        int nsweeps, int first_axis, float *fo, float *inter0, float *inter1)
+{
+    constexpr int P = KickCube<N>::P;
+    const size_t smem = (size_t)N * N * P * sizeof(float);
+    const int threads = KickCube<N>::NT;
+    long long grid = 0;
+    cudaError_t e;
+    if (nsweeps == 6 && first_axis == 0 && !inter0 && !inter1) {
+        e = kick_grid(c, k_kick6<N>, threads, smem, grid);
+        if (e != cudaSuccess) return e;
+        k_kick6<N><<<(unsigned)grid, threads, smem, c->stream>>>(f, ca, cb, c->np, &c->sc->lost,
+                                                                  fo ? fo : f);
+        return cudaGetLastError();
+    }
+    e = kick_grid(c, k_kick_fast<N>, threads, smem, grid);
+    if (e != cudaSuccess) return e;
+    k_kick_fast<N><<<(unsigned)grid, threads, smem, c->stream>>>(
+        f, ca, cb, nsweeps, first_axis, c->np, &c->sc->lost, fo ? fo : f, inter0, inter1);
     return cudaGetLastError();
 }
 
@@ -586,6 +804,24 @@ cudaError_t launch_drift_fast(vp_ctx *c, void *f, int axis, const void *coef, do
     case 48: return drift_fast_n<float, 48>(c, (float *)f, axis, cf, nullptr, 0, o);
     default: return drift_fast_n<float, 64>(c, (float *)f, axis, cf, nullptr, 0, o);
     }
+}
+
+// 1 if the fused z + y drift handles this grid (FP32, N_y = N_z in {16, 32},
+// velocity chunks inside one vz row, zero-shift drift)
+int vp_drift_yz_ok(const vp_ctx *c)
+{
+    if (c->isdouble || c->n[1] != c->n[2]) return 0;
+    const int n = c->n[1];
+    if (n != 16 && n != 32) return 0;
+    const int vc = 512 / n;
+    return c->nv[2] % vc == 0 && c->n[0] <= 65535 && c->nvc / vc <= 0x7fffffffLL;
+}
+
+cudaError_t launch_drift_yz(vp_ctx *c, const void *f, const void *coef, void *fo)
+{
+    if (c->n[1] == 32)
+        return drift_yz_n<32>(c, (const float *)f, (const LineCoef<float> *)coef, (float *)fo);
+    return drift_yz_n<16>(c, (const float *)f, (const LineCoef<float> *)coef, (float *)fo);
 }
 
 cudaError_t launch_rho_finish(vp_ctx *c, const double *part, int nparts, double *rho)

@@ -186,6 +186,33 @@ def test_split_steps_register_kernels(dtype, tol):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("space_bc", ["periodic", "outflow"])
+@pytest.mark.parametrize("shape", [dict(n=(4, 32, 32), nv=(2, 2, 16)),
+                                   dict(n=(3, 16, 16), nv=(2, 4, 32))])
+def test_fused_yz_drift_steps(shape, space_bc):
+    """FP32 grids served by the fused z + y drift pass (N_y = N_z = 32 with
+    16-cell velocity chunks, N_y = N_z = 16 with 32-cell chunks).  The vz
+    bounds are asymmetric, so one pair of z lines straddles v_z = 0."""
+    w = I.small_maxwell(dtype="f32", space_bc=space_bc, amp=0.3, G=25.0, **shape)
+    w = w.replace(box_lo=(-0.5,) * 3, box_hi=(0.5,) * 3, vlo=(-4.0, -4.0, -4.0),
+                  vhi=(4.0, 4.0, 5.0))
+    f0 = I.initial_condition(w)
+    sim, f = gpu_sim(w, f0)
+    t = sim.step(3, sync=True)
+    got = f.cpu().numpy().astype(np.float64)
+    ref = O.Simulation(f0.astype(np.float64), O.Grid.of(w), O.Params.of(w))
+    ref.step(3)
+    assert abs(t - ref.t) <= 1e-6 * ref.t
+    assert rel_l1(got, ref.f) <= 1e-5
+    assert got.min() >= 0.0
+    e, r = sim.energy(), ref.energy()
+    assert e["M"] + e["M_out"] == pytest.approx(r[0] + r[4], rel=1e-6)
+    if space_bc == "outflow":
+        assert e["M_out"] == pytest.approx(r[4], rel=1e-4, abs=1e-9 * r[0])
+    sim.close()
+
+
+@pytest.mark.gpu
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_landau_16_20_steps(dtype):
     """The 16^3 x 16^3 Landau-damping workload, 20 steps: relative L1(f) vs
