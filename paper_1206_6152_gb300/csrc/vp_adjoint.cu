@@ -46,6 +46,8 @@ struct LineGeom {
     long long nvc;
     long long stride;             // element stride along the line
     long long nlines_inner;       // v cells (position axes) or lines per cube (velocity)
+    int pairs;                    // fix-up after the pair kernels: a z line whose pair
+                                  // partner (v ^ 1) was shifted was skipped as well
 };
 
 template <typename T>
@@ -152,36 +154,63 @@ __device__ T line_adjoint(const T *F, const T *LO, T *LI, int C, int t, int n,
 
 // generic line-adjoint kernel: blockIdx.y selects the outer index (position
 // axes) or the spatial cell (velocity axes); threads take consecutive lines
+// Blocks are virtual: block vb = (bx, by) with bx = vb % vgx, by = vb / vgx,
+// vb = blockIdx.x + k gridDim.x, so that the fix-up pass after the register
+// kernels (only_shifted) can run on a small grid.
+template <typename T>
+__device__ void sweep_adjoint_block(const AdjArgs<T> &A, const LineGeom &g, const int *only_shifted,
+                                    long long bx, long long by, T *F, T *LO, T *LI, double *red);
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_sweep_adjoint(AdjArgs<T> A, LineGeom g,
-                                                      const int *only_shifted)
+                                                      const int *only_shifted, long long vgx,
+                                                      long long vtotal)
 {
     // after the register kernel: nothing to do unless it skipped a line
     if (only_shifted && *only_shifted == 0) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int C = blockDim.x;
-    const int n = g.n;
     T *F = reinterpret_cast<T *>(smem_raw);
-    T *LO = F + n * C;
-    T *LI = LO + n * C;
+    T *LO = F + g.n * C;
+    T *LI = LO + g.n * C;
     __shared__ double red[32];
+    for (long long vb = blockIdx.x; vb < vtotal; vb += gridDim.x) {
+        sweep_adjoint_block<T>(A, g, only_shifted, vb % vgx, vb / vgx, F, LO, LI, red);
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__device__ void sweep_adjoint_block(const AdjArgs<T> &A, const LineGeom &g, const int *only_shifted,
+                                    long long bx, long long by, T *F, T *LO, T *LI, double *red)
+{
+    const int C = blockDim.x;
+    const int n = g.n;
     const int t = threadIdx.x;
-    const long long w = (long long)blockIdx.x * C + t;
+    const long long w = bx * C + t;
     bool active = w < g.nlines_inner;
     long long base;
     LineCoef<T> cf;
     if (g.axis < 3) {
-        const int o = blockIdx.y;
-        const long long cell0 = (long long)(o / g.od) * g.m1 + (long long)(o % g.od) * g.m2;
+        const long long o = by;
+        const long long cell0 = (o / g.od) * g.m1 + (o % g.od) * g.m2;
         base = cell0 * g.nvc + w;
         if (active) cf = A.coef[(int)((w / A.va_stride) % A.va_n)];
     } else {
-        const long long cell = blockIdx.y;
+        const long long cell = by;
         const long long voff = (w / g.wdiv) * g.wmul_hi + (w % g.wdiv) * g.wmul_lo;
         base = cell * g.nvc + voff;
         cf = A.coef[cell * 3 + (g.axis - 3)];
     }
-    if (only_shifted && active && (cf.code >> 1) == 0) active = false;
+    if (only_shifted && active) {
+        bool shifted = (cf.code >> 1) != 0;
+        if (!shifted && g.pairs && g.axis == 2) {
+            const long long wp = w ^ 1;
+            if (wp < g.nlines_inner)
+                shifted = (A.coef[(int)((wp / A.va_stride) % A.va_n)].code >> 1) != 0;
+        }
+        if (!shifted) active = false;
+    }
     for (int j = 0; j < n; ++j) {
         F[j * C + t] = active ? A.fin[base + j * g.stride] : T(0);
         LO[j * C + t] = active ? A.lam[base + j * g.stride] : T(0);
@@ -193,7 +222,7 @@ __global__ void __launch_bounds__(128) k_sweep_adjoint(AdjArgs<T> A, LineGeom g,
     }
     if (A.lam_g) {
         da = block_sum(da, red);
-        if (t == 0 && da != 0.0) atomicAdd(A.lam_g + blockIdx.y, da * A.dalpha_scale);
+        if (t == 0 && da != 0.0) atomicAdd(A.lam_g + by, da * A.dalpha_scale);
     }
 }
 
@@ -230,19 +259,37 @@ __global__ void k_real_to_complex(const double *__restrict__ in, double2 *__rest
     if (t < n) out[t] = make_double2(in[t], 0.0);
 }
 
-// lam_f += dvol_v * lam_rho[cell] (lam_rho read from the box part of the
-// real part of cbuf)
-template <typename T>
-__global__ void k_broadcast_add(T *__restrict__ lam_f, const double2 *__restrict__ cbuf,
-                                long long nvc, int n1, int n2, int f1, int f2, double dvol_v,
-                                long long ncells)
+// bc[cell] = dvol_v * lam_rho[cell], lam_rho read from the box part of the
+// real part of cbuf
+__global__ void k_bc_box(const double2 *__restrict__ cbuf, double *__restrict__ bc, int n1, int n2,
+                         int f1, int f2, double dvol_v, long long np)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ncells) return;
-    const long long cell = t / nvc;
-    const int k = (int)(cell % n2), j = (int)((cell / n2) % n1), i = (int)(cell / ((long long)n1 * n2));
-    const double v = cbuf[((long long)i * f1 + j) * f2 + k].x * dvol_v;
-    lam_f[t] = (T)((double)lam_f[t] + v);
+    if (t >= np) return;
+    const int k = (int)(t % n2), j = (int)((t / n2) % n1), i = (int)(t / ((long long)n1 * n2));
+    bc[t] = cbuf[((long long)i * f1 + j) * f2 + k].x * dvol_v;
+}
+
+// lam_f[cell, v] += bc[cell]
+template <typename T>
+__global__ void __launch_bounds__(256) k_broadcast_box(T *__restrict__ lam_f,
+                                                      const double *__restrict__ bc, long long nvc,
+                                                      long long np)
+{
+    for (long long cell = blockIdx.x; cell < np; cell += gridDim.x) {
+        const double v = bc[cell];
+        T *q = lam_f + cell * nvc;
+        for (long long e = threadIdx.x; e < nvc; e += blockDim.x) q[e] = (T)((double)q[e] + v);
+    }
+}
+
+template <typename T>
+cudaError_t launch_broadcast(vp_ctx *c, const double *bc, T *lam)
+{
+    long long grid = 8LL * vp_sm_count();
+    if (grid > c->np) grid = c->np;
+    k_broadcast_box<T><<<(unsigned)grid, 256, 0, c->stream>>>(lam, bc, c->nvc, c->np);
+    return cudaGetLastError();
 }
 
 // lam_f = scale * w[cell] broadcast over velocity, w = phi (kind 0) or
@@ -443,13 +490,16 @@ cudaError_t launch_adjoint_fast(vp_ctx *c, const AdjArgs<T> &A, const LineGeom &
     }
 }
 
+// bc (position x only): add the density broadcast dvol_v lam_rho[cell] to
+// lam before the sweep's adjoint
 template <typename T>
 cudaError_t sweep_adjoint_t(vp_ctx *c, const T *fin, T *lam, int axis, const LineCoef<T> *coef,
-                            double *lam_g, double dalpha_scale)
+                            double *lam_g, double dalpha_scale, const double *bc = nullptr)
 {
     LineGeom g;
     AdjArgs<T> A;
     g.axis = axis;
+    g.pairs = 0;
     g.nvc = c->nvc;
     A.fin = fin;
     A.lam = lam;
@@ -488,14 +538,32 @@ cudaError_t sweep_adjoint_t(vp_ctx *c, const T *fin, T *lam, int axis, const Lin
     cudaError_t e = cudaFuncSetAttribute(k_sweep_adjoint<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    if (vp_adjoint_fast_ok(c, axis)) {
+    const long long vtotal = (long long)grid.x * grid.y;
+    bool fast = false;
+    if constexpr (sizeof(T) == 4) {
+        if (vp_adjoint_pairs_ok(c, axis)) {
+            e = launch_adjoint_pairs(c, fin, lam, axis, coef, lam_g, dalpha_scale, bc);
+            if (e != cudaSuccess) return e;
+            fast = true;
+            g.pairs = 1;
+        }
+    }
+    if (bc && !fast) {
+        if ((e = launch_broadcast(c, bc, lam)) != cudaSuccess) return e;
+    }
+    if (!fast && vp_adjoint_fast_ok(c, axis)) {
         e = launch_adjoint_fast<T>(c, A, g, grid);
         if (e != cudaSuccess) return e;
-        // lines the register kernel skipped (whole-cell shifts), if any
-        k_sweep_adjoint<T><<<grid, C, smem, c->stream>>>(A, g, c->adj_flag);
+        fast = true;
+    }
+    if (fast) {
+        // lines the register kernels skipped (whole-cell shifts), if any
+        long long small = 4LL * vp_sm_count();
+        if (small > vtotal) small = vtotal;
+        k_sweep_adjoint<T><<<(unsigned)small, C, smem, c->stream>>>(A, g, c->adj_flag, grid.x, vtotal);
         return cudaGetLastError();
     }
-    k_sweep_adjoint<T><<<grid, C, smem, c->stream>>>(A, g, nullptr);
+    k_sweep_adjoint<T><<<(unsigned)vtotal, C, smem, c->stream>>>(A, g, nullptr, grid.x, vtotal);
     return cudaGetLastError();
 }
 
@@ -540,13 +608,14 @@ __global__ void k_set(double *p, double v) { *p = v; }
 
 }  // namespace
 
-cudaError_t launch_drift_adjoint(vp_ctx *c, const void *fin, void *lam, int axis, const void *coef)
+cudaError_t launch_drift_adjoint(vp_ctx *c, const void *fin, void *lam, int axis, const void *coef,
+                                 const double *bc)
 {
     if (c->isdouble)
         return sweep_adjoint_t<double>(c, (const double *)fin, (double *)lam, axis,
-                                       (const LineCoef<double> *)coef, nullptr, 0.0);
+                                       (const LineCoef<double> *)coef, nullptr, 0.0, bc);
     return sweep_adjoint_t<float>(c, (const float *)fin, (float *)lam, axis,
-                                  (const LineCoef<float> *)coef, nullptr, 0.0);
+                                  (const LineCoef<float> *)coef, nullptr, 0.0, bc);
 }
 
 cudaError_t launch_kick_adjoint(vp_ctx *c, const void *fin, void *lam, int vaxis, const void *coef,
@@ -560,8 +629,10 @@ cudaError_t launch_kick_adjoint(vp_ctx *c, const void *fin, void *lam, int vaxis
                                   (const LineCoef<float> *)coef, lam_g, scale);
 }
 
-// lam_f += R^T P^T F^T lam_g
-cudaError_t launch_field_adjoint(vp_ctx *c, const double *lam_g, void *lam_f)
+// lam_f += R^T P^T F^T lam_g.  With defer, the density cotangent times
+// dvol_v is left in c->rho2 (box layout) for the next sweep adjoint to add
+// instead of being broadcast here.
+cudaError_t launch_field_adjoint(vp_ctx *c, const double *lam_g, void *lam_f, bool defer)
 {
     const int T = 256;
     double *lam_phi = c->phi;   // scratch: the stored potential is recomputed by the next solve
@@ -577,13 +648,12 @@ cudaError_t launch_field_adjoint(vp_ctx *c, const double *lam_g, void *lam_f)
     if ((e = launch_green_mul(c)) != cudaSuccess) return e;
     for (int a = 0; a < 3; ++a)
         if ((e = launch_fft(c, c->cbuf, a, 1)) != cudaSuccess) return e;
-    if (c->isdouble)
-        k_broadcast_add<double><<<nblk(c->ncells, T), T, 0, c->stream>>>(
-            (double *)lam_f, c->cbuf, c->nvc, c->n[1], c->n[2], c->fn[1], c->fn[2], c->dvol_v, c->ncells);
-    else
-        k_broadcast_add<float><<<nblk(c->ncells, T), T, 0, c->stream>>>(
-            (float *)lam_f, c->cbuf, c->nvc, c->n[1], c->n[2], c->fn[1], c->fn[2], c->dvol_v, c->ncells);
-    return cudaGetLastError();
+    k_bc_box<<<nblk(c->np, T), T, 0, c->stream>>>(c->cbuf, c->rho2, c->n[1], c->n[2], c->fn[1],
+                                                  c->fn[2], c->dvol_v, c->np);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (defer) return cudaSuccess;
+    if (c->isdouble) return launch_broadcast<double>(c, c->rho2, (double *)lam_f);
+    return launch_broadcast<float>(c, c->rho2, (float *)lam_f);
 }
 
 extern "C" {
@@ -601,7 +671,7 @@ int vp_sweep_adjoint(vp_ctx *c, int axis, double tau, const void *f_in, void *la
     VP_CUDA_TRY(cudaGetLastError());
     if (axis < 3) {
         VP_CUDA_TRY(launch_coef_drift(c, tau_ptr, 1.0, c->coef_drift));
-        VP_CUDA_TRY(launch_drift_adjoint(c, f_in, lambda, axis, c->coef_drift));
+        VP_CUDA_TRY(launch_drift_adjoint(c, f_in, lambda, axis, c->coef_drift, nullptr));
     } else {
         VP_CUDA_TRY(launch_coef_kick(c, c->g, tau_ptr, 1.0, c->coef_kick1));
         VP_CUDA_TRY(launch_kick_adjoint(c, f_in, lambda, axis - 3, c->coef_kick1, tau, lambda_g));
@@ -612,7 +682,7 @@ int vp_sweep_adjoint(vp_ctx *c, int axis, double tau, const void *f_in, void *la
 int vp_field_adjoint(vp_ctx *c, const double *lambda_g, void *lambda_f)
 {
     if (!c || !lambda_g || !lambda_f) return VP_ERR_ARG;
-    VP_CUDA_TRY(launch_field_adjoint(c, lambda_g, lambda_f));
+    VP_CUDA_TRY(launch_field_adjoint(c, lambda_g, lambda_f, false));
     return VP_OK;
 }
 
@@ -682,11 +752,13 @@ int vp_adjoint_step(vp_ctx *c, const void *f_start, const double *g_start, void 
     // K2 (vz, vy, vx) reversed; its g-cotangent is added to lambda_g^{n+1}
     for (int va = 2; va >= 0; --va)
         VP_CUDA_TRY(launch_kick_adjoint(c, S[6 + va], lambda_f, va, c->coef_kick2, 0.5 * dt, lambda_g));
-    // g^{n+1} = field(f_b)
-    VP_CUDA_TRY(launch_field_adjoint(c, lambda_g, lambda_f));
+    // g^{n+1} = field(f_b); its density broadcast is added by the x-drift
+    // adjoint as it loads lambda_f
+    VP_CUDA_TRY(launch_field_adjoint(c, lambda_g, lambda_f, true));
     // drift x, y, z reversed
     for (int k = 5; k >= 3; --k)
-        VP_CUDA_TRY(launch_drift_adjoint(c, S[k], lambda_f, 5 - k, c->coef_drift));
+        VP_CUDA_TRY(launch_drift_adjoint(c, S[k], lambda_f, 5 - k, c->coef_drift,
+                                         k == 5 ? c->rho2 : nullptr));
     // K1 reversed; its g-cotangent is that of g^n
     VP_CUDA_TRY(cudaMemsetAsync(lambda_g, 0, sizeof(double) * 3 * c->np, c->stream));
     for (int va = 2; va >= 0; --va)

@@ -1,0 +1,484 @@
+// vp_adjoint_fast.cu -- FP32 register-line adjoint sweeps for line lengths
+// 16 and 32 (zero whole-cell shift): the transpose of the forward kernels of
+// vp_sweep_fast.cu with their own limiter arms.
+//
+// Forward (vp_line.cuh), in the upwind frame of a line with F = 2 f_inf,
+// h_j = -f_j / F and r3 = 3 / F:
+//   u1_j = r3 f_j + h_{j+1},  u2_j = r3 f_j + h_{j-1},
+//   s1 = sat(u1), s2 = sat(u2),
+//   E+ = 2 f_j - F s1,  E- = F s2 - 2 f_j,
+//   phi_j = c0 f_j + c1 E+ + c2 E-,   out_j = f_j - phi_j + phi_{j-1}.
+// The E+ arm is interior iff sat(u1) == u1 (0 <= u1 <= 1, the arm of
+// clamp(f_{j+1} - f_j, -2 (f_inf - f_j), 2 f_j) that returns the difference
+// itself); the same for E- with u2.  With the arms frozen, and with
+// mu_j = l_{j+1} - l_j, a = c1 mu, b = c2 mu, I1 = [E+ interior],
+// I2 = [E- interior]:
+//   dl_j     += (c0 + 2 c1 - 2 c2) mu - 3 a I1 + 3 b I2,
+//   dl_{j+1} += a I1,     dl_{j-1} -= b I2,
+//   l_F      += a (u1 I1 - s1) + b (s2 - u2 I2)    (dE+/dF, dE-/dF),
+// and l_F reaches the line maximum (2 l_F on f_inf) at its first position
+// in upwind order.  The velocity sweeps also return
+//   d/dbeta = sum_j mu_j (f_j + c1'(beta) E+ + c2'(beta) E-).
+// The limiter values are the forward kernels' own (same F, h, r3 and
+// saturating FMAs), so the arms are those the forward pass took.
+//
+// Kernels:
+//  * k_adjoint_pairs: two lines per thread (adjacent vz for the vx and vy
+//    sweeps, adjacent velocity cells for the drifts), packed f32x2, state
+//    and cotangent read straight from global memory (a warp reads two
+//    128-byte rows per load).  The x-drift adjoint can add the broadcast of
+//    the density cotangent on load.
+//  * k_adjoint_rows: the vz sweep; each warp stages 32 rows of the state and
+//    of the cotangent in shared memory with coalesced 16-byte loads, one row
+//    per lane, and writes the rows back the same way.
+#include <cuda_runtime.h>
+
+#include "vp_device.cuh"
+#include "vp_internal.cuh"
+#include "vp_line.cuh"
+
+using namespace vpline;
+
+int vp_sm_count();
+
+namespace {
+
+template <typename V>
+struct AdjW {
+    V K0, c1, c2, dc1, dc2;    // K0 = c0 + 2 (c1 - c2); dc = dc/dbeta
+    V F, ninvF, r3;
+};
+
+__device__ __forceinline__ float sel1(bool p) { return p ? 1.f : 0.f; }
+
+template <typename V>
+struct AOps;
+template <>
+struct AOps<float2> {
+    __device__ __forceinline__ static float2 eq(float2 a, float2 b)
+    {
+        return make_float2(sel1(a.x == b.x), sel1(a.y == b.y));
+    }
+    __device__ __forceinline__ static float2 fsat(float2 a, float2 b, float2 c)
+    {
+        return make_float2(fmasat(a.x, b.x, c.x), fmasat(a.y, b.y, c.y));
+    }
+};
+template <>
+struct AOps<float> {
+    __device__ __forceinline__ static float eq(float a, float b) { return sel1(a == b); }
+    __device__ __forceinline__ static float fsat(float a, float b, float c) { return fmasat(a, b, c); }
+};
+
+__device__ __forceinline__ void adj_weights1(const LineCoef<float> &cf, float finf, float &K0,
+                                             float &c1, float &c2, float &dc1, float &dc2,
+                                             float &F, float &ninvF)
+{
+    float A1, A2;
+    weights1<float>(cf.c0, cf.c1, cf.c2, cf.code & 1, finf, K0, A1, A2, ninvF);
+    const float beta = cf.c0;
+    c1 = cf.c1;
+    c2 = cf.c2;
+    dc1 = (2.f - 6.f * beta + 3.f * beta * beta) * (1.f / 6.f);
+    dc2 = (1.f - 3.f * beta * beta) * (1.f / 6.f);
+    F = finf + finf;
+}
+
+__device__ __forceinline__ AdjW<float2> adj_weights(const LineCoef<float> &ca,
+                                                    const LineCoef<float> &cb, float2 finf)
+{
+    AdjW<float2> w;
+    adj_weights1(ca, finf.x, w.K0.x, w.c1.x, w.c2.x, w.dc1.x, w.dc2.x, w.F.x, w.ninvF.x);
+    adj_weights1(cb, finf.y, w.K0.y, w.c1.y, w.c2.y, w.dc1.y, w.dc2.y, w.F.y, w.ninvF.y);
+    w.r3 = __fmul2_rn(w.ninvF, make_float2(-3.f, -3.f));
+    return w;
+}
+
+__device__ __forceinline__ AdjW<float> adj_weights(const LineCoef<float> &cf, float finf)
+{
+    AdjW<float> w;
+    adj_weights1(cf, finf, w.K0, w.c1, w.c2, w.dc1, w.dc2, w.F, w.ninvF);
+    w.r3 = w.ninvF * -3.f;
+    return w;
+}
+
+// Cotangent of the zero-shift update of the line f (read-only) given the
+// output cotangent l, which is overwritten with the input cotangent (without
+// the f_inf term: l_F is returned for the caller to place).  Array index of
+// upwind position j: j (u > 0) or N - 1 - j (u < 0).
+template <typename V, int N, bool PERIODIC, bool NEG, bool DB>
+__device__ __forceinline__ void adjoint_line(const V (&f)[N], V (&l)[N], const AdjW<V> &w, V &lF,
+                                             V &db)
+{
+    typedef VOps<V> O;
+    typedef AOps<V> A;
+#define IX(j) (NEG ? N - 1 - (j) : (j))
+    const V z = O::zero();
+    const V three = O::splat(3.f), mone = O::splat(-1.f);
+    const V lo0 = l[IX(0)];
+    const V h0 = O::mul(f[IX(0)], w.ninvF);
+    V hprev = PERIODIC ? O::mul(f[IX(N - 1)], w.ninvF) : z;
+    V hcur = h0;
+    V pend = z, carry = z, t2first = z;
+    lF = z;
+    db = z;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const V f0 = f[IX(j)];
+        const V hnext = (j + 1 < N) ? O::mul(f[IX(j + 1 < N ? j + 1 : 0)], w.ninvF)
+                                    : (PERIODIC ? h0 : z);
+        const V lo = j == 0 ? lo0 : l[IX(j)];
+        const V ln = (j + 1 < N) ? l[IX(j + 1 < N ? j + 1 : 0)] : (PERIODIC ? lo0 : z);
+        const V mu = O::sub(ln, lo);
+        const V u1 = O::fma(f0, w.r3, hnext);
+        const V u2 = O::fma(f0, w.r3, hprev);
+        const V s1 = A::fsat(f0, w.r3, hnext);
+        const V s2 = A::fsat(f0, w.r3, hprev);
+        const V i1 = A::eq(s1, u1), i2 = A::eq(s2, u2);
+        const V a = O::mul(w.c1, mu), b = O::mul(w.c2, mu);
+        const V t1 = O::mul(a, i1), t2 = O::mul(b, i2);
+        const V l0 = O::fma(w.K0, mu, O::mul(three, O::sub(t2, t1)));
+        if (j >= 1) l[IX(j >= 1 ? j - 1 : 0)] = O::sub(pend, t2);
+        else t2first = t2;
+        pend = O::add(O::add(lo, carry), l0);
+        carry = t1;
+        lF = O::fma(a, O::fma(u1, i1, O::mul(s1, mone)), lF);      // a (u1 I1 - s1)
+        lF = O::fma(b, O::fma(O::mul(u2, mone), i2, s2), lF);      // b (s2 - u2 I2)
+        if (DB) {
+            const V two_f = O::add(f0, f0);
+            const V ep = O::fma(O::mul(w.F, mone), s1, two_f);      // 2 f - F s1
+            const V em = O::fma(w.F, s2, O::mul(two_f, mone));      // F s2 - 2 f
+            V e = O::fma(w.dc1, ep, f0);
+            e = O::fma(w.dc2, em, e);
+            db = O::fma(mu, e, db);
+        }
+        hprev = hcur;
+        hcur = hnext;
+    }
+    l[IX(N - 1)] = pend;
+    if (PERIODIC) {
+        l[IX(N - 1)] = O::sub(l[IX(N - 1)], t2first);
+        l[IX(0)] = O::add(l[IX(0)], carry);
+    }
+#undef IX
+}
+
+// first position in upwind order of the maximum m of the line v (array index)
+template <int N>
+__device__ __forceinline__ int first_max(const float (&v)[N], float m, bool neg)
+{
+    int a = 0;
+    if (!neg) {
+#pragma unroll
+        for (int j = N - 1; j >= 0; --j) a = v[j] == m ? j : a;
+    } else {
+#pragma unroll
+        for (int j = 0; j < N; ++j) a = v[j] == m ? j : a;
+    }
+    return a;
+}
+
+template <int N>
+__device__ __forceinline__ int2 first_max2(const float2 (&x)[N], float2 m, bool neg)
+{
+    int ax = 0, ay = 0;
+    if (!neg) {
+#pragma unroll
+        for (int j = N - 1; j >= 0; --j) {
+            ax = x[j].x == m.x ? j : ax;
+            ay = x[j].y == m.y ? j : ay;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            ax = x[j].x == m.x ? j : ax;
+            ay = x[j].y == m.y ? j : ay;
+        }
+    }
+    return make_int2(ax, ay);
+}
+
+// one scalar line of a pair (component c) whose directions differ
+template <int N, bool PERIODIC>
+__device__ __forceinline__ float adjoint_scalar(const float (&f)[N], float (&l)[N],
+                                                const LineCoef<float> &cf, bool db_on,
+                                                int &arg, float &lfinf)
+{
+    const float finf = line_max(f);
+    const AdjW<float> w = adj_weights(cf, finf);
+    float lF, db;
+    if (cf.code & 1) {
+        if (db_on) adjoint_line<float, N, PERIODIC, true, true>(f, l, w, lF, db);
+        else adjoint_line<float, N, PERIODIC, true, false>(f, l, w, lF, db);
+    } else {
+        if (db_on) adjoint_line<float, N, PERIODIC, false, true>(f, l, w, lF, db);
+        else adjoint_line<float, N, PERIODIC, false, false>(f, l, w, lF, db);
+    }
+    arg = first_max<N>(f, finf, cf.code & 1);
+    lfinf = 2.f * lF;
+    return (cf.code & 1) ? -db : db;
+}
+
+struct PairGeom {
+    int axis;                  // 0..5
+    long long nvc;
+    // drift axes: outer index o -> base cell (o / od) m1 + (o % od) m2
+    long long cell_stride;
+    int od;
+    long long m1, m2;
+    int va_stride, va_n;       // velocity index along the axis: (v / va_stride) % va_n
+    long long units;           // line pairs per outer index (drift) or per cube (kick)
+    long long per_part;        // units per CTA (drift)
+    // kick axes: pair p -> voff = (p / pd) pm_hi + 2 (p % pd), element stride vstride
+    int pd;
+    long long pm_hi, vstride;
+};
+
+// DB: the velocity sweeps' beta derivative; BC: add dvol_v lam_rho[cell] to
+// the cotangent on load (the density broadcast of the field adjoint)
+// MIXED: the two lines of a pair may travel in opposite directions (z drift,
+// where they differ in v_z); then they are done as two scalar lines
+template <int N, bool PERIODIC, bool DB, bool BC, bool MIXED>
+__global__ void __launch_bounds__(128) k_adjoint_pairs(const float *__restrict__ fin,
+                                                      float *__restrict__ lam,
+                                                      const LineCoef<float> *__restrict__ coef,
+                                                      PairGeom g, const double *__restrict__ bc,
+                                                      double *__restrict__ lam_g, double scale,
+                                                      int *skipped)
+{
+    __shared__ double red[32];
+    const int t = threadIdx.x;
+    long long base, u0, u1, stride, cell0 = 0;
+    if (g.axis < 3) {
+        const int o = blockIdx.y;
+        cell0 = (long long)(o / g.od) * g.m1 + (long long)(o % g.od) * g.m2;
+        base = cell0 * g.nvc;
+        stride = g.cell_stride * g.nvc;
+        u0 = (long long)blockIdx.x * g.per_part;
+        u1 = u0 + g.per_part;
+        if (u1 > g.units) u1 = g.units;
+    } else {
+        base = (long long)blockIdx.y * g.nvc;
+        stride = g.vstride;
+        u0 = (long long)blockIdx.x * blockDim.x;
+        u1 = u0 + blockDim.x;
+        if (u1 > g.units) u1 = g.units;
+    }
+    float da = 0.f;
+    for (long long u = u0 + t; u < u1; u += blockDim.x) {
+        long long off;
+        LineCoef<float> ca, cb;
+        if (g.axis < 3) {
+            const long long v = 2 * u;
+            off = base + v;
+            ca = coef[(int)((v / g.va_stride) % g.va_n)];
+            cb = coef[(int)(((v + 1) / g.va_stride) % g.va_n)];
+        } else {
+            off = base + (u / g.pd) * g.pm_hi + 2 * (u % g.pd);
+            ca = coef[blockIdx.y * 3 + (g.axis - 3)];
+            cb = ca;
+        }
+        if ((ca.code >> 1) != 0 || (cb.code >> 1) != 0) {
+            atomicExch(skipped, 1);
+            continue;
+        }
+        float2 f[N], l[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            f[j] = *reinterpret_cast<const float2 *>(fin + off + j * stride);
+            l[j] = *reinterpret_cast<const float2 *>(lam + off + j * stride);
+        }
+        if constexpr (BC) {
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                const float b = (float)bc[cell0 + j * g.cell_stride];
+                l[j].x += b;
+                l[j].y += b;
+            }
+        }
+        int ax, ay;
+        float lfx, lfy;
+        if (!MIXED || (ca.code & 1) == (cb.code & 1)) {
+            const float2 finf = line_max(f);
+            const AdjW<float2> w = adj_weights(ca, cb, finf);
+            float2 lF, db;
+            const bool neg = ca.code & 1;
+            if (neg) adjoint_line<float2, N, PERIODIC, true, DB>(f, l, w, lF, db);
+            else adjoint_line<float2, N, PERIODIC, false, DB>(f, l, w, lF, db);
+            const int2 a2 = first_max2<N>(f, finf, neg);
+            ax = a2.x;
+            ay = a2.y;
+            lfx = 2.f * lF.x;
+            lfy = 2.f * lF.y;
+            if (DB) da += neg ? -(db.x + db.y) : db.x + db.y;
+        } else if constexpr (MIXED) {
+            float fx[N], fy[N], lx[N], ly[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                fx[j] = f[j].x; fy[j] = f[j].y;
+                lx[j] = l[j].x; ly[j] = l[j].y;
+            }
+            const float dx = adjoint_scalar<N, PERIODIC>(fx, lx, ca, DB, ax, lfx);
+            const float dy = adjoint_scalar<N, PERIODIC>(fy, ly, cb, DB, ay, lfy);
+            if (DB) da += dx + dy;
+#pragma unroll
+            for (int j = 0; j < N; ++j) l[j] = make_float2(lx[j], ly[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) *reinterpret_cast<float2 *>(lam + off + j * stride) = l[j];
+        lam[off + ax * stride] += lfx;
+        lam[off + ay * stride + 1] += lfy;
+    }
+    if (DB) {
+        const double s = block_sum((double)da, red);
+        if (t == 0 && s != 0.0) atomicAdd(lam_g + blockIdx.y, s * scale);
+    }
+}
+
+// vz sweep of FP32 cubes of edge N (16 or 32): warp units of 32 rows
+template <int N>
+__global__ void __launch_bounds__(128) k_adjoint_rows(const float *__restrict__ fin,
+                                                     float *__restrict__ lam,
+                                                     const LineCoef<float> *__restrict__ coef,
+                                                     long long np, double *__restrict__ lam_g,
+                                                     double scale, int *skipped)
+{
+    constexpr int P = N + 4, Q = N / 4, UPC = N * N / 32;   // pitch, chunks per row, units per cube
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *tf = reinterpret_cast<float *>(smem_raw) + warp * 2 * 32 * P;
+    float *tl = tf + 32 * P;
+    const long long unit = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (unit >= np * UPC) return;
+    const long long cell = unit / UPC;
+    const LineCoef<float> cf = coef[cell * 3 + 2];
+    if ((cf.code >> 1) != 0) {
+        if (lane == 0) atomicExch(skipped, 1);
+        return;
+    }
+    const long long off = unit * 32 * N;          // 32 contiguous rows
+#pragma unroll
+    for (int e = lane; e < 32 * Q; e += 32) {
+        const int r = e / Q, c = 4 * (e % Q);
+        *reinterpret_cast<float4 *>(tf + r * P + c) = *reinterpret_cast<const float4 *>(fin + off + r * N + c);
+        *reinterpret_cast<float4 *>(tl + r * P + c) = *reinterpret_cast<const float4 *>(lam + off + r * N + c);
+    }
+    __syncwarp();
+    float f[N], l[N];
+#pragma unroll
+    for (int c = 0; c < N; c += 4) {
+        const float4 a = *reinterpret_cast<const float4 *>(tf + lane * P + c);
+        const float4 b = *reinterpret_cast<const float4 *>(tl + lane * P + c);
+        f[c] = a.x; f[c + 1] = a.y; f[c + 2] = a.z; f[c + 3] = a.w;
+        l[c] = b.x; l[c + 1] = b.y; l[c + 2] = b.z; l[c + 3] = b.w;
+    }
+    int arg;
+    float lfinf;
+    const float db = adjoint_scalar<N, false>(f, l, cf, true, arg, lfinf);
+#pragma unroll
+    for (int c = 0; c < N; c += 4)
+        *reinterpret_cast<float4 *>(tl + lane * P + c) = make_float4(l[c], l[c + 1], l[c + 2], l[c + 3]);
+    tl[lane * P + arg] += lfinf;
+    __syncwarp();
+#pragma unroll
+    for (int e = lane; e < 32 * Q; e += 32) {
+        const int r = e / Q, c = 4 * (e % Q);
+        *reinterpret_cast<float4 *>(lam + off + r * N + c) = *reinterpret_cast<const float4 *>(tl + r * P + c);
+    }
+    if (!lam_g) return;
+    float s = db;
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+    if (lane == 0 && s != 0.f) atomicAdd(lam_g + cell, (double)s * scale);
+}
+
+template <int N, bool PERIODIC>
+cudaError_t pairs_n(vp_ctx *c, const float *fin, float *lam, const LineCoef<float> *coef,
+                    const PairGeom &g, dim3 grid, const double *bc, double *lam_g, double scale)
+{
+    const bool db = g.axis >= 3 && lam_g;
+    int *sk = c->adj_flag;
+    if (db)
+        k_adjoint_pairs<N, PERIODIC, true, false, false><<<grid, 128, 0, c->stream>>>(
+            fin, lam, coef, g, bc, lam_g, scale, sk);
+    else if (bc)
+        k_adjoint_pairs<N, PERIODIC, false, true, false><<<grid, 128, 0, c->stream>>>(
+            fin, lam, coef, g, bc, lam_g, scale, sk);
+    else if (g.axis == 2)
+        k_adjoint_pairs<N, PERIODIC, false, false, true><<<grid, 128, 0, c->stream>>>(
+            fin, lam, coef, g, bc, lam_g, scale, sk);
+    else
+        k_adjoint_pairs<N, PERIODIC, false, false, false><<<grid, 128, 0, c->stream>>>(
+            fin, lam, coef, g, bc, lam_g, scale, sk);
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t rows_n(vp_ctx *c, const float *fin, float *lam, const LineCoef<float> *coef,
+                   double *lam_g, double scale)
+{
+    constexpr int P = N + 4;
+    const size_t smem = 4 * 2 * 32 * P * sizeof(float);
+    const long long units = c->np * (N * N / 32);
+    k_adjoint_rows<N><<<(unsigned)((units + 3) / 4), 128, smem, c->stream>>>(fin, lam, coef, c->np,
+                                                                            lam_g, scale, c->adj_flag);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int vp_adjoint_pairs_ok(const vp_ctx *c, int axis)
+{
+    if (c->isdouble || !c->adj_flag) return 0;
+    if (axis < 3) {
+        const int n = c->n[axis];
+        return (n == 16 || n == 32) && c->nvc % 2 == 0 && c->np / n <= 65535;
+    }
+    const int n = c->nv[0];
+    return n == c->nv[1] && n == c->nv[2] && (n == 16 || n == 32) && c->np <= 65535;
+}
+
+cudaError_t launch_adjoint_pairs(vp_ctx *c, const void *fin_, void *lam_, int axis,
+                                 const void *coef_, double *lam_g, double scale, const double *bc)
+{
+    const float *fin = (const float *)fin_;
+    float *lam = (float *)lam_;
+    const LineCoef<float> *coef = (const LineCoef<float> *)coef_;
+    cudaError_t e = cudaMemsetAsync(c->adj_flag, 0, sizeof(int), c->stream);
+    if (e != cudaSuccess) return e;
+    PairGeom g{};
+    g.axis = axis;
+    g.nvc = c->nvc;
+    if (axis < 3) {
+        const int n = c->n[axis];
+        if (axis == 0) { g.cell_stride = (long long)c->n[1] * c->n[2]; g.od = 1; g.m1 = 1; g.m2 = 0; }
+        else if (axis == 1) { g.cell_stride = c->n[2]; g.od = c->n[2]; g.m1 = (long long)c->n[1] * c->n[2]; g.m2 = 1; }
+        else { g.cell_stride = 1; g.od = 1; g.m1 = c->n[2]; g.m2 = 0; }
+        g.va_stride = axis == 0 ? c->nv[1] * c->nv[2] : (axis == 1 ? c->nv[2] : 1);
+        g.va_n = c->nv[axis];
+        g.units = c->nvc / 2;
+        const long long outer = c->np / n;
+        long long nparts = (4LL * 4 * vp_sm_count() + outer - 1) / outer;
+        const long long maxparts = (g.units + 127) / 128;
+        if (nparts > maxparts) nparts = maxparts;
+        if (nparts < 1) nparts = 1;
+        g.per_part = (g.units + nparts - 1) / nparts;
+        const dim3 grid((unsigned)nparts, (unsigned)outer);
+        const LineCoef<float> *cf = coef + (size_t)axis * c->maxnv;
+        if (c->periodic_space)
+            return n == 32 ? pairs_n<32, true>(c, fin, lam, cf, g, grid, bc, nullptr, 0.0)
+                           : pairs_n<16, true>(c, fin, lam, cf, g, grid, bc, nullptr, 0.0);
+        return n == 32 ? pairs_n<32, false>(c, fin, lam, cf, g, grid, bc, nullptr, 0.0)
+                       : pairs_n<16, false>(c, fin, lam, cf, g, grid, bc, nullptr, 0.0);
+    }
+    const int va = axis - 3, n = c->nv[0];
+    double *lg = lam_g ? lam_g + (size_t)va * c->np : nullptr;
+    if (va == 2) return n == 32 ? rows_n<32>(c, fin, lam, coef, lg, scale)
+                                : rows_n<16>(c, fin, lam, coef, lg, scale);
+    g.pd = n / 2;
+    g.pm_hi = va == 0 ? n : (long long)n * n;
+    g.vstride = va == 0 ? (long long)n * n : n;
+    g.units = (long long)n * n / 2;
+    const dim3 grid((unsigned)((g.units + 127) / 128), (unsigned)c->np);
+    return n == 32 ? pairs_n<32, false>(c, fin, lam, coef, g, grid, nullptr, lg, scale)
+                   : pairs_n<16, false>(c, fin, lam, coef, g, grid, nullptr, lg, scale);
+}

@@ -154,7 +154,16 @@ cudaError_t launch_green_mul(vp_ctx *c);
 double vp_drift_alpha_bound(const vp_ctx *c, double tau);
 
 // adjoint (vp_adjoint.cu)
-cudaError_t launch_drift_adjoint(vp_ctx *c, const void *fin, void *lam, int axis, const void *coef);
+// bc (x axis only, may be null): dvol_v lam_rho per spatial cell, added to
+// lam before the adjoint (the deferred density broadcast of the field adjoint)
+cudaError_t launch_drift_adjoint(vp_ctx *c, const void *fin, void *lam, int axis, const void *coef,
+                                 const double *bc);
 cudaError_t launch_kick_adjoint(vp_ctx *c, const void *fin, void *lam, int vaxis, const void *coef,
                                 double tau, double *lam_g);
-cudaError_t launch_field_adjoint(vp_ctx *c, const double *lam_g, void *lam_f);
+// defer: leave dvol_v lam_rho in c->rho2 instead of adding it to lam_f
+cudaError_t launch_field_adjoint(vp_ctx *c, const double *lam_g, void *lam_f, bool defer);
+// FP32 packed register-line adjoint sweeps (line lengths 16/32, zero
+// whole-cell shift; skipped lines set c->adj_flag)
+int vp_adjoint_pairs_ok(const vp_ctx *c, int axis);
+cudaError_t launch_adjoint_pairs(vp_ctx *c, const void *fin, void *lam, int axis, const void *coef,
+                                 double *lam_g, double scale, const double *bc);

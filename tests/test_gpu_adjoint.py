@@ -61,11 +61,19 @@ def test_sweep_adjoint_matches_oracle(space_bc):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("dtype,shape", [("f64", dict(n=(16, 16, 16), nv=(16, 16, 16))),
-                                         ("f32", dict(n=(16, 32, 16), nv=(16, 16, 32)))])
-def test_register_adjoint_sweeps_match_oracle(dtype, shape):
-    """Line lengths served by the register-line adjoint kernel."""
-    w = I.small_maxwell(dtype=dtype, amp=0.3, **shape)
+@pytest.mark.parametrize("dtype,shape,space_bc", [
+    ("f64", dict(n=(16, 16, 16), nv=(16, 16, 16)), "periodic"),
+    ("f32", dict(n=(16, 32, 16), nv=(16, 16, 32)), "periodic"),
+    ("f32", dict(n=(16, 32, 16), nv=(16, 16, 32)), "outflow"),
+    ("f32", dict(n=(4, 2, 2), nv=(32, 32, 32)), "periodic"),
+    ("f32", dict(n=(4, 4, 2), nv=(16, 16, 16)), "periodic"),
+])
+def test_register_adjoint_sweeps_match_oracle(dtype, shape, space_bc):
+    """Line lengths served by the register-line adjoint kernels: FP64 lines
+    of 16; FP32 packed line pairs of 16 and 32 along position axes (both
+    boundary kinds, and pairs of z lines with different speeds) and along vx
+    and vy of 16^3 and 32^3 cubes, and the warp-staged vz rows."""
+    w = I.small_maxwell(dtype=dtype, amp=0.3, space_bc=space_bc, **shape)
     w = w.replace(box_lo=(-0.5,) * 3, box_hi=(0.5,) * 3)
     grid = O.Grid.of(w)
     rng = np.random.default_rng(9)
@@ -84,7 +92,8 @@ def test_register_adjoint_sweeps_match_oracle(dtype, shape):
             ds = np.zeros(int(np.prod(w.n)))
             f64 = f0.astype(np.float64)
             if axis < 3:
-                O.sweep_adjoint(f64, ref, axis, grid.vc(axis), tau, grid.dx[axis], True, None)
+                O.sweep_adjoint(f64, ref, axis, grid.vc(axis), tau, grid.dx[axis],
+                                space_bc == "periodic", None)
             else:
                 O.sweep_adjoint(f64, ref, axis, acc[axis - 3], tau, grid.dv[axis - 3], False, ds)
             got = lam.cpu().numpy().astype(np.float64)
@@ -120,6 +129,31 @@ def test_adjoint_step_matches_oracle(bc):
     got_f, got_g = lam_f.cpu().numpy(), lam_g.cpu().numpy()
     assert np.abs(got_f - rf).max() <= 1e-9 * np.abs(rf).max()
     assert np.abs(got_g - rg).max() <= 1e-9 * np.abs(rg).max()
+    sim.close()
+
+
+@pytest.mark.gpu
+def test_adjoint_step_fp32_register_kernels_match_oracle():
+    """FP32 adjoint step on a grid served by the packed kernels (x lines of
+    16 with the density broadcast added on load, 16^3 velocity cubes)
+    against the FP64 oracle's adjoint step."""
+    w = I.small_maxwell(n=(16, 2, 2), nv=(16, 16, 16), dtype="f32", amp=0.2, G=20.0)
+    w = w.replace(dt_fixed=0.01, box_lo=(-0.5, -0.05, -0.05), box_hi=(0.5, 0.05, 0.05))
+    grid = O.Grid.of(w)
+    rng = np.random.default_rng(4)
+    f0 = (I.initial_condition(w, np.float64) * (1 + 0.2 * rng.random(w.shape))).astype(np.float32)
+    sim, f = gpu_sim(w, f0)
+    g0 = sim.field()[2]
+    lam_f = torch.from_numpy(rng.normal(size=w.shape).astype(np.float32)).to(DEV)
+    lam_g = torch.from_numpy(rng.normal(size=(3,) + w.n)).to(DEV)
+    lf0, lg0 = lam_f.cpu().numpy().astype(np.float64), lam_g.cpu().numpy()
+    sim.adjoint_step(torch.from_numpy(f0).to(DEV), g0, lam_f, lam_g)
+    f64 = f0.astype(np.float64)
+    osim = O.Simulation(f64, grid, O.Params.of(w))
+    rf, rg = O.adjoint_step(osim, f64, osim.g, lf0, lg0)
+    got_f, got_g = lam_f.cpu().numpy().astype(np.float64), lam_g.cpu().numpy()
+    assert np.abs(got_f - rf).sum() / np.abs(rf).sum() <= 2e-5
+    assert np.abs(got_g - rg).sum() / np.abs(rg).sum() <= 2e-5
     sim.close()
 
 
