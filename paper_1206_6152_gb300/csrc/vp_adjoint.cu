@@ -48,6 +48,8 @@ struct LineGeom {
     long long nlines_inner;       // v cells (position axes) or lines per cube (velocity)
     int pairs;                    // fix-up after the pair kernels: a z line whose pair
                                   // partner (v ^ 1) was shifted was skipped as well
+    int cube3;                    // fix-up after the fused kick adjoint: every line of a
+                                  // cube with a shift on any velocity axis
 };
 
 template <typename T>
@@ -204,6 +206,10 @@ __device__ void sweep_adjoint_block(const AdjArgs<T> &A, const LineGeom &g, cons
     }
     if (only_shifted && active) {
         bool shifted = (cf.code >> 1) != 0;
+        if (!shifted && g.cube3 && g.axis >= 3) {
+            const LineCoef<T> *cc = A.coef + by * 3;
+            shifted = ((cc[0].code >> 1) | (cc[1].code >> 1) | (cc[2].code >> 1)) != 0;
+        }
         if (!shifted && g.pairs && g.axis == 2) {
             const long long wp = w ^ 1;
             if (wp < g.nlines_inner)
@@ -492,14 +498,17 @@ cudaError_t launch_adjoint_fast(vp_ctx *c, const AdjArgs<T> &A, const LineGeom &
 
 // bc (position x only): add the density broadcast dvol_v lam_rho[cell] to
 // lam before the sweep's adjoint
+// cube3: only the fix-up pass after the fused kick adjoint
 template <typename T>
 cudaError_t sweep_adjoint_t(vp_ctx *c, const T *fin, T *lam, int axis, const LineCoef<T> *coef,
-                            double *lam_g, double dalpha_scale, const double *bc = nullptr)
+                            double *lam_g, double dalpha_scale, const double *bc = nullptr,
+                            int cube3 = 0)
 {
     LineGeom g;
     AdjArgs<T> A;
     g.axis = axis;
     g.pairs = 0;
+    g.cube3 = cube3;
     g.nvc = c->nvc;
     A.fin = fin;
     A.lam = lam;
@@ -539,6 +548,12 @@ cudaError_t sweep_adjoint_t(vp_ctx *c, const T *fin, T *lam, int axis, const Lin
                                          (int)smem);
     if (e != cudaSuccess) return e;
     const long long vtotal = (long long)grid.x * grid.y;
+    if (cube3) {
+        long long small = 4LL * vp_sm_count();
+        if (small > vtotal) small = vtotal;
+        k_sweep_adjoint<T><<<(unsigned)small, C, smem, c->stream>>>(A, g, c->adj_flag, grid.x, vtotal);
+        return cudaGetLastError();
+    }
     bool fast = false;
     if constexpr (sizeof(T) == 4) {
         if (vp_adjoint_pairs_ok(c, axis)) {
@@ -627,6 +642,26 @@ cudaError_t launch_kick_adjoint(vp_ctx *c, const void *fin, void *lam, int vaxis
                                        (const LineCoef<double> *)coef, lam_g, scale);
     return sweep_adjoint_t<float>(c, (const float *)fin, (float *)lam, 3 + vaxis,
                                   (const LineCoef<float> *)coef, lam_g, scale);
+}
+
+// the three velocity-sweep adjoints of a half kick: vz (input sc), vy (sb),
+// vx (sa), in that order
+static int kick_adjoint3(vp_ctx *c, const void *sa, const void *sb, const void *sc, void *lam,
+                  const void *coef, double tau, double *lam_g)
+{
+    const void *S[3] = {sa, sb, sc};
+    if (vp_kick_adjoint3_ok(c)) {
+        VP_CUDA_TRY(launch_kick_adjoint3(c, sa, sb, sc, lam, coef, lam_g, tau));
+        // cubes it skipped (whole-cell shifts), if any
+        for (int va = 2; va >= 0; --va)
+            VP_CUDA_TRY(sweep_adjoint_t<float>(c, (const float *)S[va], (float *)lam, 3 + va,
+                                               (const LineCoef<float> *)coef, lam_g,
+                                               tau / c->dv[va], nullptr, 1));
+        return VP_OK;
+    }
+    for (int va = 2; va >= 0; --va)
+        VP_CUDA_TRY(launch_kick_adjoint(c, S[va], lam, va, coef, tau, lam_g));
+    return VP_OK;
 }
 
 // lam_f += R^T P^T F^T lam_g.  With defer, the density cotangent times
@@ -723,7 +758,6 @@ int vp_adjoint_step(vp_ctx *c, const void *f_start, const double *g_start, void 
     if (!(c->cfg.dt_fixed > 0.0)) return VP_ERR_STATE;
     TRY(ensure_adjoint_scratch(c));
     const double dt = c->cfg.dt_fixed;
-    const size_t bytes = (size_t)c->ncells * c->esize;
     void **S = c->adj_states;
     double *tau_ptr = &c->sc->pad[2];
     k_set<<<1, 1, 0, c->stream>>>(tau_ptr, dt);
@@ -732,26 +766,36 @@ int vp_adjoint_step(vp_ctx *c, const void *f_start, const double *g_start, void 
     void *k1 = c->adj_f;
     VP_CUDA_TRY(launch_coef_kick(c, g_start, tau_ptr, 0.5, k1));
     VP_CUDA_TRY(launch_coef_drift(c, tau_ptr, 1.0, c->coef_drift));
-    // forward replay, keeping every sweep input: S[0] = f^n, S[k+1] = sweep k of S[k]
-    VP_CUDA_TRY(cudaMemcpyAsync(S[0], f_start, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    // forward replay, keeping every sweep input: S[0] = f^n, S[k+1] = sweep k
+    // of S[k]; S[0] is f_start itself
+    const void *S0 = f_start;
     const double amax = vp_drift_alpha_bound(c, dt);
-    for (int k = 0; k < 8; ++k) {
-        if (k < 3) {
-            VP_CUDA_TRY(launch_sweep_into(c, S[k], S[k + 1], 3 + k, k1, amax));
-        } else if (k < 6) {
-            VP_CUDA_TRY(launch_sweep_into(c, S[k], S[k + 1], 5 - k, c->coef_drift, amax));
-            if (k == 5) {
-                VP_CUDA_TRY(launch_density(c, S[6], c->rho2));
-                VP_CUDA_TRY(launch_field_solve(c, c->rho2, c->adj_g));
-                VP_CUDA_TRY(launch_coef_kick(c, c->adj_g, tau_ptr, 0.5, c->coef_kick2));
-            }
-        } else {
-            VP_CUDA_TRY(launch_sweep_into(c, S[k], S[k + 1], 3 + (k - 6), c->coef_kick2, amax));
-        }
+    const bool kfast = vp_kick_fast_ok(c);
+    if (kfast) {
+        VP_CUDA_TRY(launch_kick_fast(c, (void *)S0, k1, nullptr, 3, 0, S[3], S[1], S[2]));
+    } else {
+        for (int k = 0; k < 3; ++k)
+            VP_CUDA_TRY(launch_sweep_into(c, k ? S[k] : S0, S[k + 1], 3 + k, k1, amax));
+    }
+    VP_CUDA_TRY(launch_sweep_into(c, S[3], S[4], 2, c->coef_drift, amax));
+    VP_CUDA_TRY(launch_sweep_into(c, S[4], S[5], 1, c->coef_drift, amax));
+    if (c->rho_part && vp_rho_fuse_ok(c) && amax < 1.0) {
+        VP_CUDA_TRY(launch_drift_fast(c, S[5], 0, c->coef_drift, c->rho_part, S[6]));
+        VP_CUDA_TRY(launch_rho_finish(c, c->rho_part, c->rho_nparts, c->rho2));
+    } else {
+        VP_CUDA_TRY(launch_sweep_into(c, S[5], S[6], 0, c->coef_drift, amax));
+        VP_CUDA_TRY(launch_density(c, S[6], c->rho2));
+    }
+    VP_CUDA_TRY(launch_field_solve(c, c->rho2, c->adj_g));
+    VP_CUDA_TRY(launch_coef_kick(c, c->adj_g, tau_ptr, 0.5, c->coef_kick2));
+    if (kfast) {
+        VP_CUDA_TRY(launch_kick_fast(c, S[6], c->coef_kick2, nullptr, 2, 0, S[8], S[7], nullptr));
+    } else {
+        VP_CUDA_TRY(launch_sweep_into(c, S[6], S[7], 3, c->coef_kick2, amax));
+        VP_CUDA_TRY(launch_sweep_into(c, S[7], S[8], 4, c->coef_kick2, amax));
     }
     // K2 (vz, vy, vx) reversed; its g-cotangent is added to lambda_g^{n+1}
-    for (int va = 2; va >= 0; --va)
-        VP_CUDA_TRY(launch_kick_adjoint(c, S[6 + va], lambda_f, va, c->coef_kick2, 0.5 * dt, lambda_g));
+    TRY(kick_adjoint3(c, S[6], S[7], S[8], lambda_f, c->coef_kick2, 0.5 * dt, lambda_g));
     // g^{n+1} = field(f_b); its density broadcast is added by the x-drift
     // adjoint as it loads lambda_f
     VP_CUDA_TRY(launch_field_adjoint(c, lambda_g, lambda_f, true));
@@ -761,8 +805,7 @@ int vp_adjoint_step(vp_ctx *c, const void *f_start, const double *g_start, void 
                                          k == 5 ? c->rho2 : nullptr));
     // K1 reversed; its g-cotangent is that of g^n
     VP_CUDA_TRY(cudaMemsetAsync(lambda_g, 0, sizeof(double) * 3 * c->np, c->stream));
-    for (int va = 2; va >= 0; --va)
-        VP_CUDA_TRY(launch_kick_adjoint(c, S[va], lambda_f, va, k1, 0.5 * dt, lambda_g));
+    TRY(kick_adjoint3(c, S0, S[1], S[2], lambda_f, k1, 0.5 * dt, lambda_g));
     return VP_OK;
 }
 

@@ -31,6 +31,9 @@
 //  * k_adjoint_rows: the vz sweep; each warp stages 32 rows of the state and
 //    of the cotangent in shared memory with coalesced 16-byte loads, one row
 //    per lane, and writes the rows back the same way.
+//  * k_kick_adjoint_zy: the vz and then the vy adjoint of a half kick on the
+//    same staged rows (a warp holds whole vx planes), followed by the vx
+//    adjoint as line pairs: the cotangent crosses HBM twice for three sweeps.
 #include <cuda_runtime.h>
 
 #include "vp_device.cuh"
@@ -163,6 +166,59 @@ __device__ __forceinline__ void adjoint_line(const V (&f)[N], V (&l)[N], const A
 #undef IX
 }
 
+// As adjoint_line, with the output cotangent read from memory (lsrc, stride
+// ls elements of V) and the input cotangent written to memory (ldst, stride
+// ld; may equal lsrc: every element is read before it is overwritten).
+// Outflow boundaries (velocity lines).
+template <typename V, int N, bool NEG, bool DB>
+__device__ __forceinline__ void adjoint_line_mem(const V (&f)[N], const V *lsrc, int ls, V *ldst,
+                                                 int ld, const AdjW<V> &w, V &lF, V &db)
+{
+    typedef VOps<V> O;
+    typedef AOps<V> A;
+#define IX(j) (NEG ? N - 1 - (j) : (j))
+    const V z = O::zero();
+    const V three = O::splat(3.f), mone = O::splat(-1.f);
+    V hprev = z, hcur = O::mul(f[IX(0)], w.ninvF);
+    V pend = z, carry = z;
+    V lo = lsrc[IX(0) * ls];
+    lF = z;
+    db = z;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const V f0 = f[IX(j)];
+        const V hnext = (j + 1 < N) ? O::mul(f[IX(j + 1 < N ? j + 1 : 0)], w.ninvF) : z;
+        const V ln = (j + 1 < N) ? lsrc[IX(j + 1 < N ? j + 1 : 0) * ls] : z;
+        const V mu = O::sub(ln, lo);
+        const V u1 = O::fma(f0, w.r3, hnext);
+        const V u2 = O::fma(f0, w.r3, hprev);
+        const V s1 = A::fsat(f0, w.r3, hnext);
+        const V s2 = A::fsat(f0, w.r3, hprev);
+        const V i1 = A::eq(s1, u1), i2 = A::eq(s2, u2);
+        const V a = O::mul(w.c1, mu), b = O::mul(w.c2, mu);
+        const V t1 = O::mul(a, i1), t2 = O::mul(b, i2);
+        const V l0 = O::fma(w.K0, mu, O::mul(three, O::sub(t2, t1)));
+        if (j >= 1) ldst[IX(j >= 1 ? j - 1 : 0) * ld] = O::sub(pend, t2);
+        pend = O::add(O::add(lo, carry), l0);
+        carry = t1;
+        lF = O::fma(a, O::fma(u1, i1, O::mul(s1, mone)), lF);
+        lF = O::fma(b, O::fma(O::mul(u2, mone), i2, s2), lF);
+        if (DB) {
+            const V two_f = O::add(f0, f0);
+            const V ep = O::fma(O::mul(w.F, mone), s1, two_f);
+            const V em = O::fma(w.F, s2, O::mul(two_f, mone));
+            V e = O::fma(w.dc1, ep, f0);
+            e = O::fma(w.dc2, em, e);
+            db = O::fma(mu, e, db);
+        }
+        hprev = hcur;
+        hcur = hnext;
+        lo = ln;
+    }
+    ldst[IX(N - 1) * ld] = pend;
+#undef IX
+}
+
 // first position in upwind order of the maximum m of the line v (array index)
 template <int N>
 __device__ __forceinline__ int first_max(const float (&v)[N], float m, bool neg)
@@ -232,6 +288,7 @@ struct PairGeom {
     // kick axes: pair p -> voff = (p / pd) pm_hi + 2 (p % pd), element stride vstride
     int pd;
     long long pm_hi, vstride;
+    int cube3;                 // kick axes: skip a cube with a shift on any velocity axis
 };
 
 // DB: the velocity sweeps' beta derivative; BC: add dvol_v lam_rho[cell] to
@@ -277,6 +334,10 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(const float *__restrict__
             off = base + (u / g.pd) * g.pm_hi + 2 * (u % g.pd);
             ca = coef[blockIdx.y * 3 + (g.axis - 3)];
             cb = ca;
+            if (g.cube3) {
+                const LineCoef<float> *cc = coef + blockIdx.y * 3;
+                cb.code |= (cc[0].code | cc[1].code | cc[2].code) & ~1;
+            }
         }
         if ((ca.code >> 1) != 0 || (cb.code >> 1) != 0) {
             atomicExch(skipped, 1);
@@ -391,6 +452,96 @@ __global__ void __launch_bounds__(128) k_adjoint_rows(const float *__restrict__ 
     if (lane == 0 && s != 0.f) atomicAdd(lam_g + cell, (double)s * scale);
 }
 
+// The vz and vy adjoints of a half kick in one pass: each warp takes 32
+// rows of one cube (one vx plane for N = 32, two for N = 16), stages the
+// cotangent and the vz input of those rows in shared memory with coalesced
+// 16-byte loads, does the vz adjoint one row per lane, then the vy adjoint
+// one column per lane (the vy input read straight from global memory, 128
+// contiguous bytes per warp load, the cotangent from shared memory), and
+// writes the rows back.  A cube with a whole-cell shift on any velocity
+// axis is skipped (all three of its sweeps go to the fix-up pass).
+template <int N>
+__global__ void __launch_bounds__(128) k_kick_adjoint_zy(const float *__restrict__ sb,
+                                                        const float *__restrict__ sc,
+                                                        float *__restrict__ lam,
+                                                        const LineCoef<float> *__restrict__ coef,
+                                                        long long np, double *__restrict__ lam_g,
+                                                        double scale_y, double scale_z,
+                                                        int *skipped)
+{
+    constexpr int P = N + 4, Q = N / 4, UPC = N * N / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *tl = reinterpret_cast<float *>(smem_raw) + warp * 2 * 32 * P;
+    float *ts = tl + 32 * P;
+    const long long unit = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (unit >= np * UPC) return;
+    const long long cell = unit / UPC;
+    const LineCoef<float> cx = coef[cell * 3], cy = coef[cell * 3 + 1], cz = coef[cell * 3 + 2];
+    if (((cx.code | cy.code | cz.code) >> 1) != 0) {
+        if (lane == 0) atomicExch(skipped, 1);
+        return;
+    }
+    const long long off = unit * 32 * N;
+#pragma unroll 4
+    for (int e = lane; e < 32 * Q; e += 32) {
+        const int r = e / Q, c = 4 * (e % Q);
+        *reinterpret_cast<float4 *>(tl + r * P + c) = *reinterpret_cast<const float4 *>(lam + off + r * N + c);
+        *reinterpret_cast<float4 *>(ts + r * P + c) = *reinterpret_cast<const float4 *>(sc + off + r * N + c);
+    }
+    __syncwarp();
+    float dz, dy;
+    {
+        float f[N], l[N];
+#pragma unroll
+        for (int c = 0; c < N; c += 4) {
+            const float4 a = *reinterpret_cast<const float4 *>(ts + lane * P + c);
+            const float4 b = *reinterpret_cast<const float4 *>(tl + lane * P + c);
+            f[c] = a.x; f[c + 1] = a.y; f[c + 2] = a.z; f[c + 3] = a.w;
+            l[c] = b.x; l[c + 1] = b.y; l[c + 2] = b.z; l[c + 3] = b.w;
+        }
+        int arg;
+        float lfinf;
+        dz = adjoint_scalar<N, false>(f, l, cz, true, arg, lfinf);
+#pragma unroll
+        for (int c = 0; c < N; c += 4)
+            *reinterpret_cast<float4 *>(tl + lane * P + c) = make_float4(l[c], l[c + 1], l[c + 2], l[c + 3]);
+        tl[lane * P + arg] += lfinf;
+    }
+    __syncwarp();
+    {
+        const int pl = lane / N, k = lane % N;
+        const float *g = sb + off + (long long)pl * N * N + k;
+        float f[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) f[j] = g[j * N];
+        const float finf = line_max(f);
+        const AdjW<float> w = adj_weights(cy, finf);
+        float *L = tl + pl * N * P + k;
+        float lF, db;
+        const bool neg = cy.code & 1;
+        if (neg) adjoint_line_mem<float, N, true, true>(f, L, P, L, P, w, lF, db);
+        else adjoint_line_mem<float, N, false, true>(f, L, P, L, P, w, lF, db);
+        L[first_max<N>(f, finf, neg) * P] += 2.f * lF;
+        dy = neg ? -db : db;
+    }
+    __syncwarp();
+#pragma unroll 4
+    for (int e = lane; e < 32 * Q; e += 32) {
+        const int r = e / Q, c = 4 * (e % Q);
+        *reinterpret_cast<float4 *>(lam + off + r * N + c) = *reinterpret_cast<const float4 *>(tl + r * P + c);
+    }
+    if (!lam_g) return;
+    for (int d = 16; d > 0; d >>= 1) {
+        dz += __shfl_xor_sync(0xffffffffu, dz, d);
+        dy += __shfl_xor_sync(0xffffffffu, dy, d);
+    }
+    if (lane == 0) {
+        if (dz != 0.f) atomicAdd(lam_g + 2 * np + cell, (double)dz * scale_z);
+        if (dy != 0.f) atomicAdd(lam_g + np + cell, (double)dy * scale_y);
+    }
+}
+
 template <int N, bool PERIODIC>
 cudaError_t pairs_n(vp_ctx *c, const float *fin, float *lam, const LineCoef<float> *coef,
                     const PairGeom &g, dim3 grid, const double *bc, double *lam_g, double scale)
@@ -426,6 +577,38 @@ cudaError_t rows_n(vp_ctx *c, const float *fin, float *lam, const LineCoef<float
 
 }  // namespace
 
+int vp_kick_adjoint3_ok(const vp_ctx *c)
+{
+    const int n = c->nv[0];
+    return !c->isdouble && c->adj_flag && n == c->nv[1] && n == c->nv[2] && (n == 16 || n == 32) &&
+           c->np <= 65535;
+}
+
+// the three velocity-sweep adjoints of a half kick: sa, sb, sc the inputs
+// of the vx, vy, vz sweeps; lam_g (3 np) accumulates the g cotangent with
+// d alpha / d g = tau / dv per axis.  vz and vy in one pass, then vx.
+cudaError_t launch_kick_adjoint3(vp_ctx *c, const void *sa, const void *sb, const void *sc,
+                                 void *lam, const void *coef, double *lam_g, double tau)
+{
+    cudaError_t e = cudaMemsetAsync(c->adj_flag, 0, sizeof(int), c->stream);
+    if (e != cudaSuccess) return e;
+    const int n = c->nv[0];
+    const long long units = c->np * ((long long)n * n / 32);
+    const unsigned grid = (unsigned)((units + 3) / 4);
+    const size_t smem = (size_t)4 * 2 * 32 * (n + 4) * sizeof(float);
+    const LineCoef<float> *cf = (const LineCoef<float> *)coef;
+    if (n == 32)
+        k_kick_adjoint_zy<32><<<grid, 128, smem, c->stream>>>(
+            (const float *)sb, (const float *)sc, (float *)lam, cf, c->np, lam_g, tau / c->dv[1],
+            tau / c->dv[2], c->adj_flag);
+    else
+        k_kick_adjoint_zy<16><<<grid, 128, smem, c->stream>>>(
+            (const float *)sb, (const float *)sc, (float *)lam, cf, c->np, lam_g, tau / c->dv[1],
+            tau / c->dv[2], c->adj_flag);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_adjoint_pairs(c, sa, lam, 3, coef, lam_g, tau / c->dv[0], nullptr, 1);
+}
+
 int vp_adjoint_pairs_ok(const vp_ctx *c, int axis)
 {
     if (c->isdouble || !c->adj_flag) return 0;
@@ -438,14 +621,18 @@ int vp_adjoint_pairs_ok(const vp_ctx *c, int axis)
 }
 
 cudaError_t launch_adjoint_pairs(vp_ctx *c, const void *fin_, void *lam_, int axis,
-                                 const void *coef_, double *lam_g, double scale, const double *bc)
+                                 const void *coef_, double *lam_g, double scale, const double *bc,
+                                 int cube3)
 {
     const float *fin = (const float *)fin_;
     float *lam = (float *)lam_;
     const LineCoef<float> *coef = (const LineCoef<float> *)coef_;
-    cudaError_t e = cudaMemsetAsync(c->adj_flag, 0, sizeof(int), c->stream);
-    if (e != cudaSuccess) return e;
+    if (!cube3) {
+        cudaError_t e = cudaMemsetAsync(c->adj_flag, 0, sizeof(int), c->stream);
+        if (e != cudaSuccess) return e;
+    }
     PairGeom g{};
+    g.cube3 = cube3;
     g.axis = axis;
     g.nvc = c->nvc;
     if (axis < 3) {
@@ -457,11 +644,10 @@ cudaError_t launch_adjoint_pairs(vp_ctx *c, const void *fin_, void *lam_, int ax
         g.va_n = c->nv[axis];
         g.units = c->nvc / 2;
         const long long outer = c->np / n;
-        long long nparts = (4LL * 4 * vp_sm_count() + outer - 1) / outer;
-        const long long maxparts = (g.units + 127) / 128;
-        if (nparts > maxparts) nparts = maxparts;
-        if (nparts < 1) nparts = 1;
-        g.per_part = (g.units + nparts - 1) / nparts;
+        // one line pair per thread: a thread holds two lines of f and of the
+        // cotangent, so latency is hidden by many resident CTAs
+        g.per_part = 128;
+        const long long nparts = (g.units + 127) / 128;
         const dim3 grid((unsigned)nparts, (unsigned)outer);
         const LineCoef<float> *cf = coef + (size_t)axis * c->maxnv;
         if (c->periodic_space)

@@ -165,5 +165,13 @@ cudaError_t launch_field_adjoint(vp_ctx *c, const double *lam_g, void *lam_f, bo
 // FP32 packed register-line adjoint sweeps (line lengths 16/32, zero
 // whole-cell shift; skipped lines set c->adj_flag)
 int vp_adjoint_pairs_ok(const vp_ctx *c, int axis);
+// the three velocity-sweep adjoints of a half kick in one cube pass (FP32,
+// cubic 16/32 velocity grids); cubes with a whole-cell shift on any axis
+// are skipped and set c->adj_flag
+int vp_kick_adjoint3_ok(const vp_ctx *c);
+cudaError_t launch_kick_adjoint3(vp_ctx *c, const void *sa, const void *sb, const void *sc,
+                                 void *lam, const void *coef, double *lam_g, double tau);
+// cube3 (kick axes): skip every cube with a shift on any velocity axis and
+// keep c->adj_flag as it is
 cudaError_t launch_adjoint_pairs(vp_ctx *c, const void *fin, void *lam, int axis, const void *coef,
-                                 double *lam_g, double scale, const double *bc);
+                                 double *lam_g, double scale, const double *bc, int cube3 = 0);

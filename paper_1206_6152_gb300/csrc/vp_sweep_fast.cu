@@ -231,7 +231,8 @@ __device__ __forceinline__ float sweep_pairs(float2 (&x)[N], const LineCoef<floa
 template <int N>
 __device__ __noinline__ float kick_cube_shifted(const float *g, float *go, float *cube,
                                                 const LineCoef<float> *cf, int nsweeps,
-                                                int first_axis)
+                                                int first_axis, float *inter0 = nullptr,
+                                                float *inter1 = nullptr)
 {
     constexpr int P = KickCube<N>::P;
     constexpr int NT = KickCube<N>::NT;
@@ -255,6 +256,14 @@ __device__ __noinline__ float kick_cube_shifted(const float *g, float *go, float
             lost += kick_line_shifted(base, st, N, c);
         }
         __syncthreads();
+        float *ist = sw == 0 ? inter0 : (sw == 1 ? inter1 : nullptr);
+        if (ist && sw < nsweeps - 1) {
+            for (int e = t; e < NC / 4; e += NT) {
+                const int r = (4 * e) / N, k = (4 * e) % N;
+                reinterpret_cast<float4 *>(ist)[e] = *reinterpret_cast<const float4 *>(cube + r * P + k);
+            }
+            __syncthreads();
+        }
     }
     for (int e = t; e < NC / 4; e += NT) {
         const int r = (4 * e) / N, k = (4 * e) % N;
@@ -294,7 +303,9 @@ __global__ void __launch_bounds__(KickCube<N>::NT) k_kick_fast(float *__restrict
         bool shifted = false;
         for (int sw = 0; sw < nsweeps; ++sw) shifted |= (scf[par][sw].code >> 1) != 0;
         if (shifted) {
-            lost += kick_cube_shifted<N>(g, go, cube, scf[par], nsweeps, first_axis);
+            lost += kick_cube_shifted<N>(g, go, cube, scf[par], nsweeps, first_axis,
+                                         inter0 ? inter0 + cell * (long long)NC : nullptr,
+                                         inter1 ? inter1 + cell * (long long)NC : nullptr);
             continue;
         }
         for (int sw = 0; sw < nsweeps; ++sw) {

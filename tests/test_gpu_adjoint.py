@@ -133,11 +133,14 @@ def test_adjoint_step_matches_oracle(bc):
 
 
 @pytest.mark.gpu
-def test_adjoint_step_fp32_register_kernels_match_oracle():
+@pytest.mark.parametrize("G", [20.0, 200.0])
+def test_adjoint_step_fp32_register_kernels_match_oracle(G):
     """FP32 adjoint step on a grid served by the packed kernels (x lines of
     16 with the density broadcast added on load, 16^3 velocity cubes)
-    against the FP64 oracle's adjoint step."""
-    w = I.small_maxwell(n=(16, 2, 2), nv=(16, 16, 16), dtype="f32", amp=0.2, G=20.0)
+    against the FP64 oracle's adjoint step.  With the large G the kicks
+    shift by whole cells: the replay's shifted-cube path and the adjoint's
+    fix-up pass."""
+    w = I.small_maxwell(n=(16, 2, 2), nv=(16, 16, 16), dtype="f32", amp=0.2, G=G)
     w = w.replace(dt_fixed=0.01, box_lo=(-0.5, -0.05, -0.05), box_hi=(0.5, 0.05, 0.05))
     grid = O.Grid.of(w)
     rng = np.random.default_rng(4)
@@ -152,6 +155,8 @@ def test_adjoint_step_fp32_register_kernels_match_oracle():
     osim = O.Simulation(f64, grid, O.Params.of(w))
     rf, rg = O.adjoint_step(osim, f64, osim.g, lf0, lg0)
     got_f, got_g = lam_f.cpu().numpy().astype(np.float64), lam_g.cpu().numpy()
+    if G > 100:
+        assert np.abs(osim.g).max() * 0.5 * w.dt_fixed / grid.dv[0] > 1.5   # whole-cell kicks
     assert np.abs(got_f - rf).sum() / np.abs(rf).sum() <= 2e-5
     assert np.abs(got_g - rg).sum() / np.abs(rg).sum() <= 2e-5
     sim.close()
