@@ -196,8 +196,23 @@ def jeans_profile() -> Workload:
     return jeans_c2().replace(name="jeans16x32_f32", n=(16, 16, 16))
 
 
+def jeans_slab_yz() -> Workload:
+    """A 4-plane slab (4 x 32 x 32 spatial cells) of the 32^3 x 32^3 Jeans
+    box: the fused z + y drift at its full-size line length 32, with 537 MB
+    of FP32 f (above L2), for hardware-counter captures."""
+    return jeans_c2().replace(name="jeans_slab_yz_f32", n=(4, 32, 32))
+
+
+def jeans_slab_x() -> Workload:
+    """A 32 x 8 x 8 slab of the 32^3 x 32^3 Jeans box: the x drift with the
+    fused density at line length 32, 268 MB of FP32 f (above L2)."""
+    return jeans_c2().replace(name="jeans_slab_x_f32", n=(32, 8, 8))
+
+
 WORKLOADS = {
     "jeans16x32_f32": jeans_profile,
+    "jeans_slab_yz_f32": jeans_slab_yz,
+    "jeans_slab_x_f32": jeans_slab_x,
     "landau16_f64": landau_c1,
     "jeans32_f32": jeans_c2,
     "king64x32_w6": king_c3,
