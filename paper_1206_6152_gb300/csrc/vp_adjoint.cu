@@ -645,20 +645,28 @@ cudaError_t launch_kick_adjoint(vp_ctx *c, const void *fin, void *lam, int vaxis
 }
 
 // the three velocity-sweep adjoints of a half kick: vz (input sc), vy (sb),
-// vx (sa), in that order
-static int kick_adjoint3(vp_ctx *c, const void *sa, const void *sb, const void *sc, void *lam,
-                  const void *coef, double tau, double *lam_g)
+// vx (sa), in that order.  sc may be null when the register path serves the
+// grid: the vz input is then recomputed, and for the cubes the register
+// kernels skip (whole-cell shifts) it is swept into scratch for the fix-up.
+static int kick_adjoint3(vp_ctx *c, const void *sa, const void *sb, const void *sc, void *scratch,
+                         void *lam, const void *coef, double tau, double *lam_g)
 {
-    const void *S[3] = {sa, sb, sc};
     if (vp_kick_adjoint3_ok(c)) {
-        VP_CUDA_TRY(launch_kick_adjoint3(c, sa, sb, sc, lam, coef, lam_g, tau));
-        // cubes it skipped (whole-cell shifts), if any
+        VP_CUDA_TRY(launch_kick_adjoint3(c, sa, sb, lam, coef, lam_g, tau));
+        if (!sc) {
+            VP_CUDA_TRY(launch_kick_fast(c, const_cast<void *>(sb), coef, nullptr, 1, 1, scratch,
+                                         nullptr, nullptr, c->adj_flag));
+            sc = scratch;
+        }
+        const void *S[3] = {sa, sb, sc};
         for (int va = 2; va >= 0; --va)
             VP_CUDA_TRY(sweep_adjoint_t<float>(c, (const float *)S[va], (float *)lam, 3 + va,
                                                (const LineCoef<float> *)coef, lam_g,
                                                tau / c->dv[va], nullptr, 1));
         return VP_OK;
     }
+    if (!sc) return VP_ERR_STATE;
+    const void *S[3] = {sa, sb, sc};
     for (int va = 2; va >= 0; --va)
         VP_CUDA_TRY(launch_kick_adjoint(c, S[va], lam, va, coef, tau, lam_g));
     return VP_OK;
@@ -762,23 +770,32 @@ int vp_adjoint_step(vp_ctx *c, const void *f_start, const double *g_start, void 
     double *tau_ptr = &c->sc->pad[2];
     k_set<<<1, 1, 0, c->stream>>>(tau_ptr, dt);
     VP_CUDA_TRY(cudaGetLastError());
+    // the replay's outflow is not the simulation's: keep the counter aside
+    VP_CUDA_TRY(cudaMemcpyAsync(&c->sc->pad[1], &c->sc->lost, sizeof(double),
+                                cudaMemcpyDeviceToDevice, c->stream));
     // tables of the replay: K1 from g^n, drift, K2 from the recomputed g^{n+1}
     void *k1 = c->adj_f;
     VP_CUDA_TRY(launch_coef_kick(c, g_start, tau_ptr, 0.5, k1));
     VP_CUDA_TRY(launch_coef_drift(c, tau_ptr, 1.0, c->coef_drift));
-    // forward replay, keeping every sweep input: S[0] = f^n, S[k+1] = sweep k
-    // of S[k]; S[0] is f_start itself
-    const void *S0 = f_start;
     const double amax = vp_drift_alpha_bound(c, dt);
-    const bool kfast = vp_kick_fast_ok(c);
-    if (kfast) {
-        VP_CUDA_TRY(launch_kick_fast(c, (void *)S0, k1, nullptr, 3, 0, S[3], S[1], S[2]));
+    const void *S0 = f_start;     // S[k]: input of sweep k of the step (S[0] = f^n)
+    const bool reg = vp_kick_adjoint3_ok(c);
+    // --- forward replay
+    if (reg) {
+        // K1 in one pass keeping the vx output (the vz input is recomputed)
+        VP_CUDA_TRY(launch_kick_fast(c, const_cast<void *>(S0), k1, nullptr, 3, 0, S[3], S[1], nullptr));
+    } else if (vp_kick_fast_ok(c)) {
+        VP_CUDA_TRY(launch_kick_fast(c, const_cast<void *>(S0), k1, nullptr, 3, 0, S[3], S[1], S[2]));
     } else {
         for (int k = 0; k < 3; ++k)
             VP_CUDA_TRY(launch_sweep_into(c, k ? S[k] : S0, S[k + 1], 3 + k, k1, amax));
     }
-    VP_CUDA_TRY(launch_sweep_into(c, S[3], S[4], 2, c->coef_drift, amax));
-    VP_CUDA_TRY(launch_sweep_into(c, S[4], S[5], 1, c->coef_drift, amax));
+    if (amax < 1.0 && vp_drift_yz_ok(c)) {
+        VP_CUDA_TRY(launch_drift_yz(c, S[3], c->coef_drift, S[5], S[4]));
+    } else {
+        VP_CUDA_TRY(launch_sweep_into(c, S[3], S[4], 2, c->coef_drift, amax));
+        VP_CUDA_TRY(launch_sweep_into(c, S[4], S[5], 1, c->coef_drift, amax));
+    }
     if (c->rho_part && vp_rho_fuse_ok(c) && amax < 1.0) {
         VP_CUDA_TRY(launch_drift_fast(c, S[5], 0, c->coef_drift, c->rho_part, S[6]));
         VP_CUDA_TRY(launch_rho_finish(c, c->rho_part, c->rho_nparts, c->rho2));
@@ -788,14 +805,18 @@ int vp_adjoint_step(vp_ctx *c, const void *f_start, const double *g_start, void 
     }
     VP_CUDA_TRY(launch_field_solve(c, c->rho2, c->adj_g));
     VP_CUDA_TRY(launch_coef_kick(c, c->adj_g, tau_ptr, 0.5, c->coef_kick2));
-    if (kfast) {
+    if (reg) {
+        VP_CUDA_TRY(launch_kick_fast(c, S[6], c->coef_kick2, nullptr, 1, 0, S[7]));
+    } else if (vp_kick_fast_ok(c)) {
         VP_CUDA_TRY(launch_kick_fast(c, S[6], c->coef_kick2, nullptr, 2, 0, S[8], S[7], nullptr));
     } else {
         VP_CUDA_TRY(launch_sweep_into(c, S[6], S[7], 3, c->coef_kick2, amax));
         VP_CUDA_TRY(launch_sweep_into(c, S[7], S[8], 4, c->coef_kick2, amax));
     }
-    // K2 (vz, vy, vx) reversed; its g-cotangent is added to lambda_g^{n+1}
-    TRY(kick_adjoint3(c, S[6], S[7], S[8], lambda_f, c->coef_kick2, 0.5 * dt, lambda_g));
+    // --- reverse
+    // K2 (vz, vy, vx); its g-cotangent is added to lambda_g^{n+1}
+    TRY(kick_adjoint3(c, S[6], S[7], reg ? nullptr : S[8], S[8], lambda_f, c->coef_kick2, 0.5 * dt,
+                      lambda_g));
     // g^{n+1} = field(f_b); its density broadcast is added by the x-drift
     // adjoint as it loads lambda_f
     VP_CUDA_TRY(launch_field_adjoint(c, lambda_g, lambda_f, true));
@@ -805,7 +826,9 @@ int vp_adjoint_step(vp_ctx *c, const void *f_start, const double *g_start, void 
                                          k == 5 ? c->rho2 : nullptr));
     // K1 reversed; its g-cotangent is that of g^n
     VP_CUDA_TRY(cudaMemsetAsync(lambda_g, 0, sizeof(double) * 3 * c->np, c->stream));
-    TRY(kick_adjoint3(c, S0, S[1], S[2], lambda_f, k1, 0.5 * dt, lambda_g));
+    TRY(kick_adjoint3(c, S0, S[1], reg ? nullptr : S[2], S[2], lambda_f, k1, 0.5 * dt, lambda_g));
+    VP_CUDA_TRY(cudaMemcpyAsync(&c->sc->lost, &c->sc->pad[1], sizeof(double),
+                                cudaMemcpyDeviceToDevice, c->stream));
     return VP_OK;
 }
 

@@ -54,6 +54,15 @@ struct AdjW {
 
 __device__ __forceinline__ float sel1(bool p) { return p ? 1.f : 0.f; }
 
+// forward weights of one line (as the forward kernels)
+template <typename S>
+__device__ __forceinline__ LineW<S> weights_one(const LineCoef<S> &cf, S finf)
+{
+    LineW<S> w;
+    weights1<S>(cf.c0, cf.c1, cf.c2, cf.code & 1, finf, w.K0, w.A1, w.A2, w.ninvF);
+    return w;
+}
+
 template <typename V>
 struct AOps;
 template <>
@@ -275,6 +284,23 @@ __device__ __forceinline__ float adjoint_scalar(const float (&f)[N], float (&l)[
     return (cf.code & 1) ? -db : db;
 }
 
+// a pair of lines travelling in opposite directions: two scalar adjoints,
+// out of line (the arrays are copies in local memory; rare)
+template <int N, bool PERIODIC, bool DB>
+__device__ __noinline__ float adjoint_pair_mixed(const float2 *f, float2 *l, LineCoef<float> ca,
+                                                 LineCoef<float> cb, int *arg, float *lfinf)
+{
+    float fx[N], fy[N], lx[N], ly[N];
+    for (int j = 0; j < N; ++j) {
+        fx[j] = f[j].x; fy[j] = f[j].y;
+        lx[j] = l[j].x; ly[j] = l[j].y;
+    }
+    const float dx = adjoint_scalar<N, PERIODIC>(fx, lx, ca, DB, arg[0], lfinf[0]);
+    const float dy = adjoint_scalar<N, PERIODIC>(fy, ly, cb, DB, arg[1], lfinf[1]);
+    for (int j = 0; j < N; ++j) l[j] = make_float2(lx[j], ly[j]);
+    return dx + dy;
+}
+
 struct PairGeom {
     int axis;                  // 0..5
     long long nvc;
@@ -283,6 +309,7 @@ struct PairGeom {
     int od;
     long long m1, m2;
     int va_stride, va_n;       // velocity index along the axis: (v / va_stride) % va_n
+    int zremap, nvz;           // z drift: pairs per half vz row of the warp-uniform map (0: off)
     long long units;           // line pairs per outer index (drift) or per cube (kick)
     long long per_part;        // units per CTA (drift)
     // kick axes: pair p -> voff = (p / pd) pm_hi + 2 (p % pd), element stride vstride
@@ -304,6 +331,7 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(const float *__restrict__
                                                       int *skipped)
 {
     __shared__ double red[32];
+    __shared__ float sbc[BC ? N : 1];
     const int t = threadIdx.x;
     long long base, u0, u1, stride, cell0 = 0;
     if (g.axis < 3) {
@@ -314,6 +342,10 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(const float *__restrict__
         u0 = (long long)blockIdx.x * g.per_part;
         u1 = u0 + g.per_part;
         if (u1 > g.units) u1 = g.units;
+        if constexpr (BC) {
+            if (t < N) sbc[t] = (float)bc[cell0 + t * g.cell_stride];
+            __syncthreads();
+        }
     } else {
         base = (long long)blockIdx.y * g.nvc;
         stride = g.vstride;
@@ -326,7 +358,14 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(const float *__restrict__
         long long off;
         LineCoef<float> ca, cb;
         if (g.axis < 3) {
-            const long long v = 2 * u;
+            long long v = 2 * u;
+            if (g.zremap > 0) {
+                // a warp takes the same half (the same sign of v_z) of 32 / H
+                // consecutive vz rows, H pairs each
+                const int H = g.zremap, RW = 32 / H;
+                const long long q = u % H, r1 = u / H, ri = r1 % RW, r2 = r1 / RW;
+                v = ((r2 >> 1) * RW + ri) * g.nvz + ((r2 & 1) * H + q) * 2;
+            }
             off = base + v;
             ca = coef[(int)((v / g.va_stride) % g.va_n)];
             cb = coef[(int)(((v + 1) / g.va_stride) % g.va_n)];
@@ -352,7 +391,7 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(const float *__restrict__
         if constexpr (BC) {
 #pragma unroll
             for (int j = 0; j < N; ++j) {
-                const float b = (float)bc[cell0 + j * g.cell_stride];
+                const float b = sbc[j];
                 l[j].x += b;
                 l[j].y += b;
             }
@@ -373,17 +412,17 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(const float *__restrict__
             lfy = 2.f * lF.y;
             if (DB) da += neg ? -(db.x + db.y) : db.x + db.y;
         } else if constexpr (MIXED) {
-            float fx[N], fy[N], lx[N], ly[N];
+            float2 fm[N], lm[N];
 #pragma unroll
-            for (int j = 0; j < N; ++j) {
-                fx[j] = f[j].x; fy[j] = f[j].y;
-                lx[j] = l[j].x; ly[j] = l[j].y;
-            }
-            const float dx = adjoint_scalar<N, PERIODIC>(fx, lx, ca, DB, ax, lfx);
-            const float dy = adjoint_scalar<N, PERIODIC>(fy, ly, cb, DB, ay, lfy);
-            if (DB) da += dx + dy;
+            for (int j = 0; j < N; ++j) { fm[j] = f[j]; lm[j] = l[j]; }
+            int am[2];
+            float lfm[2];
+            const float d = adjoint_pair_mixed<N, PERIODIC, DB>(fm, lm, ca, cb, am, lfm);
+            if (DB) da += d;
+            ax = am[0]; ay = am[1];
+            lfx = lfm[0]; lfy = lfm[1];
 #pragma unroll
-            for (int j = 0; j < N; ++j) l[j] = make_float2(lx[j], ly[j]);
+            for (int j = 0; j < N; ++j) l[j] = lm[j];
         }
 #pragma unroll
         for (int j = 0; j < N; ++j) *reinterpret_cast<float2 *>(lam + off + j * stride) = l[j];
@@ -453,28 +492,36 @@ __global__ void __launch_bounds__(128) k_adjoint_rows(const float *__restrict__ 
 }
 
 // The vz and vy adjoints of a half kick in one pass: each warp takes 32
-// rows of one cube (one vx plane for N = 32, two for N = 16), stages the
-// cotangent and the vz input of those rows in shared memory with coalesced
-// 16-byte loads, does the vz adjoint one row per lane, then the vy adjoint
-// one column per lane (the vy input read straight from global memory, 128
-// contiguous bytes per warp load, the cotangent from shared memory), and
-// writes the rows back.  A cube with a whole-cell shift on any velocity
-// axis is skipped (all three of its sweeps go to the fix-up pass).
+// rows of one cube (one vx plane for N = 32, two for N = 16) and stages the
+// cotangent and the vy input of those rows in shared memory with coalesced
+// 16-byte loads.  It recomputes the vz input (the forward vy sweep, one
+// column per lane, bitwise as the forward kernels), does the vz adjoint one
+// row per lane and the vy adjoint one column per lane, and writes the rows
+// back.  A cube with a whole-cell shift on any velocity axis is skipped:
+// all three of its sweeps go to the fix-up pass.  (A packed variant with two
+// rows or columns per lane needs 255 registers, leaves 8 warps per SM and
+// ran slower.)
+template <int N>
+struct KickZY {
+    static constexpr int P = N + 4, Q = N / 4, UPC = N * N / 32, WPC = 4;   // warps per CTA
+    static constexpr size_t SMEM = (size_t)WPC * 3 * 32 * P * sizeof(float);
+};
+
 template <int N>
 __global__ void __launch_bounds__(128) k_kick_adjoint_zy(const float *__restrict__ sb,
-                                                        const float *__restrict__ sc,
                                                         float *__restrict__ lam,
                                                         const LineCoef<float> *__restrict__ coef,
                                                         long long np, double *__restrict__ lam_g,
                                                         double scale_y, double scale_z,
                                                         int *skipped)
 {
-    constexpr int P = N + 4, Q = N / 4, UPC = N * N / 32;
+    constexpr int P = KickZY<N>::P, Q = KickZY<N>::Q, UPC = KickZY<N>::UPC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *tl = reinterpret_cast<float *>(smem_raw) + warp * 2 * 32 * P;
-    float *ts = tl + 32 * P;
-    const long long unit = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    float *tl = reinterpret_cast<float *>(smem_raw) + warp * 3 * 32 * P;
+    float *tb = tl + 32 * P;       // vy input rows
+    float *tc = tb + 32 * P;       // vz input rows (recomputed)
+    const long long unit = (long long)blockIdx.x * KickZY<N>::WPC + warp;
     if (unit >= np * UPC) return;
     const long long cell = unit / UPC;
     const LineCoef<float> cx = coef[cell * 3], cy = coef[cell * 3 + 1], cz = coef[cell * 3 + 2];
@@ -487,7 +534,19 @@ __global__ void __launch_bounds__(128) k_kick_adjoint_zy(const float *__restrict
     for (int e = lane; e < 32 * Q; e += 32) {
         const int r = e / Q, c = 4 * (e % Q);
         *reinterpret_cast<float4 *>(tl + r * P + c) = *reinterpret_cast<const float4 *>(lam + off + r * N + c);
-        *reinterpret_cast<float4 *>(ts + r * P + c) = *reinterpret_cast<const float4 *>(sc + off + r * N + c);
+        *reinterpret_cast<float4 *>(tb + r * P + c) = *reinterpret_cast<const float4 *>(sb + off + r * N + c);
+    }
+    __syncwarp();
+    const int pl = lane / N, k = lane % N;          // this lane's vy column
+    const bool negy = cy.code & 1;
+    {
+        float x[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) x[j] = tb[(pl * N + j) * P + k];
+        const LineW<float> w = weights_one<float>(cy, line_max(x));
+        update_line<float, N, false>(x, w, negy);
+#pragma unroll
+        for (int j = 0; j < N; ++j) tc[(pl * N + j) * P + k] = x[j];
     }
     __syncwarp();
     float dz, dy;
@@ -495,7 +554,7 @@ __global__ void __launch_bounds__(128) k_kick_adjoint_zy(const float *__restrict
         float f[N], l[N];
 #pragma unroll
         for (int c = 0; c < N; c += 4) {
-            const float4 a = *reinterpret_cast<const float4 *>(ts + lane * P + c);
+            const float4 a = *reinterpret_cast<const float4 *>(tc + lane * P + c);
             const float4 b = *reinterpret_cast<const float4 *>(tl + lane * P + c);
             f[c] = a.x; f[c + 1] = a.y; f[c + 2] = a.z; f[c + 3] = a.w;
             l[c] = b.x; l[c + 1] = b.y; l[c + 2] = b.z; l[c + 3] = b.w;
@@ -510,20 +569,17 @@ __global__ void __launch_bounds__(128) k_kick_adjoint_zy(const float *__restrict
     }
     __syncwarp();
     {
-        const int pl = lane / N, k = lane % N;
-        const float *g = sb + off + (long long)pl * N * N + k;
         float f[N];
 #pragma unroll
-        for (int j = 0; j < N; ++j) f[j] = g[j * N];
+        for (int j = 0; j < N; ++j) f[j] = tb[(pl * N + j) * P + k];
         const float finf = line_max(f);
         const AdjW<float> w = adj_weights(cy, finf);
         float *L = tl + pl * N * P + k;
         float lF, db;
-        const bool neg = cy.code & 1;
-        if (neg) adjoint_line_mem<float, N, true, true>(f, L, P, L, P, w, lF, db);
+        if (negy) adjoint_line_mem<float, N, true, true>(f, L, P, L, P, w, lF, db);
         else adjoint_line_mem<float, N, false, true>(f, L, P, L, P, w, lF, db);
-        L[first_max<N>(f, finf, neg) * P] += 2.f * lF;
-        dy = neg ? -db : db;
+        L[first_max<N>(f, finf, negy) * P] += 2.f * lF;
+        dy = negy ? -db : db;
     }
     __syncwarp();
 #pragma unroll 4
@@ -584,27 +640,33 @@ int vp_kick_adjoint3_ok(const vp_ctx *c)
            c->np <= 65535;
 }
 
-// the three velocity-sweep adjoints of a half kick: sa, sb, sc the inputs
-// of the vx, vy, vz sweeps; lam_g (3 np) accumulates the g cotangent with
-// d alpha / d g = tau / dv per axis.  vz and vy in one pass, then vx.
-cudaError_t launch_kick_adjoint3(vp_ctx *c, const void *sa, const void *sb, const void *sc,
-                                 void *lam, const void *coef, double *lam_g, double tau)
+// the three velocity-sweep adjoints of a half kick: sa, sb the inputs of
+// the vx and vy sweeps (the vz input is recomputed); lam_g (3 np)
+// accumulates the g cotangent with d alpha / d g = tau / dv per axis.  vz and
+// vy in one pass, then vx.  Skipped cubes set c->adj_flag.
+cudaError_t launch_kick_adjoint3(vp_ctx *c, const void *sa, const void *sb, void *lam,
+                                 const void *coef, double *lam_g, double tau)
 {
     cudaError_t e = cudaMemsetAsync(c->adj_flag, 0, sizeof(int), c->stream);
     if (e != cudaSuccess) return e;
     const int n = c->nv[0];
-    const long long units = c->np * ((long long)n * n / 32);
-    const unsigned grid = (unsigned)((units + 3) / 4);
-    const size_t smem = (size_t)4 * 2 * 32 * (n + 4) * sizeof(float);
     const LineCoef<float> *cf = (const LineCoef<float> *)coef;
-    if (n == 32)
-        k_kick_adjoint_zy<32><<<grid, 128, smem, c->stream>>>(
-            (const float *)sb, (const float *)sc, (float *)lam, cf, c->np, lam_g, tau / c->dv[1],
-            tau / c->dv[2], c->adj_flag);
-    else
-        k_kick_adjoint_zy<16><<<grid, 128, smem, c->stream>>>(
-            (const float *)sb, (const float *)sc, (float *)lam, cf, c->np, lam_g, tau / c->dv[1],
-            tau / c->dv[2], c->adj_flag);
+    if (n == 32) {
+        typedef KickZY<32> K;
+        const unsigned grid = (unsigned)((c->np * K::UPC + K::WPC - 1) / K::WPC);
+        if ((e = cudaFuncSetAttribute(k_kick_adjoint_zy<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)K::SMEM)) != cudaSuccess)
+            return e;
+        k_kick_adjoint_zy<32><<<grid, 32 * K::WPC, K::SMEM, c->stream>>>(
+            (const float *)sb, (float *)lam, cf, c->np, lam_g, tau / c->dv[1], tau / c->dv[2],
+            c->adj_flag);
+    } else {
+        typedef KickZY<16> K;
+        const unsigned grid = (unsigned)((c->np * K::UPC + K::WPC - 1) / K::WPC);
+        k_kick_adjoint_zy<16><<<grid, 32 * K::WPC, K::SMEM, c->stream>>>(
+            (const float *)sb, (float *)lam, cf, c->np, lam_g, tau / c->dv[1], tau / c->dv[2],
+            c->adj_flag);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return launch_adjoint_pairs(c, sa, lam, 3, coef, lam_g, tau / c->dv[0], nullptr, 1);
 }
@@ -643,6 +705,11 @@ cudaError_t launch_adjoint_pairs(vp_ctx *c, const void *fin_, void *lam_, int ax
         g.va_stride = axis == 0 ? c->nv[1] * c->nv[2] : (axis == 1 ? c->nv[2] : 1);
         g.va_n = c->nv[axis];
         g.units = c->nvc / 2;
+        g.nvz = c->nv[2];
+        if (axis == 2 && c->nv[2] % 4 == 0) {
+            const int H = c->nv[2] / 4;
+            if (32 % H == 0 && ((long long)c->nv[0] * c->nv[1]) % (2 * (32 / H)) == 0) g.zremap = H;
+        }
         const long long outer = c->np / n;
         // one line pair per thread: a thread holds two lines of f and of the
         // cotangent, so latency is hidden by many resident CTAs

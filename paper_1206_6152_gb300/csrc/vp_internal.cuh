@@ -131,14 +131,18 @@ int vp_kick_fast_ok(const vp_ctx *c);
 int vp_drift_fast_ok(const vp_ctx *c, int axis);
 int vp_rho_fuse_ok(const vp_ctx *c);
 int vp_rho_parts(vp_ctx *c);
-// fo: output array (nullptr: in place)
-// inter0/inter1: optional copies of the cube after sweeps 0 and 1
-// fused z then y drift of the whole grid (in place when fo == f)
+// fused z then y drift of the whole grid (in place when fo == f); fz, if not
+// null, also receives the z sweep's output (fz != f)
 int vp_drift_yz_ok(const vp_ctx *c);
-cudaError_t launch_drift_yz(vp_ctx *c, const void *f, const void *coef, void *fo);
+cudaError_t launch_drift_yz(vp_ctx *c, const void *f, const void *coef, void *fo,
+                            void *fz = nullptr);
+// fo: output array (nullptr: in place);
+// inter0/inter1: optional copies of the cube after sweeps 0 and 1.  gate:
+// if not null, nothing runs unless *gate != 0, and only cubes whose table
+// entries (ca, all three axes) have a whole-cell shift are swept.
 cudaError_t launch_kick_fast(vp_ctx *c, void *f, const void *ca, const void *cb, int nsweeps,
                              int first_axis, void *fo = nullptr, void *inter0 = nullptr,
-                             void *inter1 = nullptr);
+                             void *inter1 = nullptr, const int *gate = nullptr);
 cudaError_t launch_drift_fast(vp_ctx *c, void *f, int axis, const void *coef, double *rho_part,
                               void *fo = nullptr);
 // one sweep from src into dst (dst != src), used by the adjoint's replay;
@@ -169,8 +173,8 @@ int vp_adjoint_pairs_ok(const vp_ctx *c, int axis);
 // cubic 16/32 velocity grids); cubes with a whole-cell shift on any axis
 // are skipped and set c->adj_flag
 int vp_kick_adjoint3_ok(const vp_ctx *c);
-cudaError_t launch_kick_adjoint3(vp_ctx *c, const void *sa, const void *sb, const void *sc,
-                                 void *lam, const void *coef, double *lam_g, double tau);
+cudaError_t launch_kick_adjoint3(vp_ctx *c, const void *sa, const void *sb, void *lam,
+                                 const void *coef, double *lam_g, double tau);
 // cube3 (kick axes): skip every cube with a shift on any velocity axis and
 // keep c->adj_flag as it is
 cudaError_t launch_adjoint_pairs(vp_ctx *c, const void *fin, void *lam, int axis, const void *coef,

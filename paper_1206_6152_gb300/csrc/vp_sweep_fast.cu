@@ -279,8 +279,10 @@ __global__ void __launch_bounds__(KickCube<N>::NT) k_kick_fast(float *__restrict
                                                              int nsweeps, int first_axis, long long np,
                                                              double *lost_out, float *__restrict__ fo,
                                                              float *__restrict__ inter0,
-                                                             float *__restrict__ inter1)
+                                                             float *__restrict__ inter1,
+                                                             const int *gate)
 {
+    if (gate && *gate == 0) return;
     constexpr int NC = KickCube<N>::NC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *cube = reinterpret_cast<float *>(smem_raw);
@@ -292,6 +294,8 @@ __global__ void __launch_bounds__(KickCube<N>::NT) k_kick_fast(float *__restrict
     for (long long cell = blockIdx.x; cell < np; cell += gridDim.x, par ^= 1) {
         float *g = f + cell * (long long)NC;
         float *go = fo + cell * (long long)NC;          // output cube (== g in place)
+        if (gate && ((ca[cell * 3].code | ca[cell * 3 + 1].code | ca[cell * 3 + 2].code) >> 1) == 0)
+            continue;
         if (t < nsweeps) scf[par][t] = (t < 3 ? ca : cb)[cell * 3 + (first_axis + t) % 3];
         // first sweep: lines straight from global memory, issued before the
         // barrier that publishes the coefficients and retires the previous
@@ -581,7 +585,8 @@ __global__ void __launch_bounds__(DriftYZ<N>::NT) k_drift_yz(const float *__rest
                                                            const LineCoef<float> *__restrict__ cy,
                                                            long long nvc, int nvy, int nvz,
                                                            double *lost_out,
-                                                           float *__restrict__ fo)
+                                                           float *__restrict__ fo,
+                                                           float *__restrict__ fz)
 {
     constexpr int VC = DriftYZ<N>::VC, YP = DriftYZ<N>::YP, H = VC / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -599,6 +604,11 @@ __global__ void __launch_bounds__(DriftYZ<N>::NT) k_drift_yz(const float *__rest
         for (int j = 0; j < N; ++j) x[j] = *reinterpret_cast<const float2 *>(p + j * nvc);
         const LineCoef<float> ca = cz[(int)(v % nvz)], cb = cz[(int)((v + 1) % nvz)];
         lost += drift_pair<N, PERIODIC>(x, ca, cb);
+        if (fz) {                       // the z sweep's output as well (adjoint replay)
+            float *pz = fz + (x0 + (long long)r * N) * nvc + v;
+#pragma unroll
+            for (int j = 0; j < N; ++j) *reinterpret_cast<float2 *>(pz + j * nvc) = x[j];
+        }
         float *q = tile + r * YP + 2 * vp;
 #pragma unroll
         for (int j = 0; j < N; ++j) *reinterpret_cast<float2 *>(q + j * VC) = x[j];
@@ -623,7 +633,7 @@ __global__ void __launch_bounds__(DriftYZ<N>::NT) k_drift_yz(const float *__rest
 }
 
 template <int N>
-cudaError_t drift_yz_n(vp_ctx *c, const float *f, const LineCoef<float> *coef, float *fo)
+cudaError_t drift_yz_n(vp_ctx *c, const float *f, const LineCoef<float> *coef, float *fo, float *fz)
 {
     constexpr int NT = DriftYZ<N>::NT;
     const size_t smem = (size_t)N * DriftYZ<N>::YP * sizeof(float);
@@ -634,13 +644,13 @@ cudaError_t drift_yz_n(vp_ctx *c, const float *f, const LineCoef<float> *coef, f
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k_drift_yz<N, true><<<grid, NT, smem, c->stream>>>(f, cz, cy, c->nvc, c->nv[1], c->nv[2],
-                                                           &c->sc->lost, fo);
+                                                           &c->sc->lost, fo, fz);
     } else {
         cudaError_t e = cudaFuncSetAttribute(k_drift_yz<N, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k_drift_yz<N, false><<<grid, NT, smem, c->stream>>>(f, cz, cy, c->nvc, c->nv[1], c->nv[2],
-                                                            &c->sc->lost, fo);
+                                                            &c->sc->lost, fo, fz);
     }
     return cudaGetLastError();
 }
@@ -672,14 +682,15 @@ cudaError_t kick_grid(vp_ctx *c, K kern, int threads, size_t smem, long long &gr
 
 template <int N>
 cudaError_t kick_fast_n(vp_ctx *c, float *f, const LineCoef<float> *ca, const LineCoef<float> *cb,
-                        int nsweeps, int first_axis, float *fo, float *inter0, float *inter1)
+                        int nsweeps, int first_axis, float *fo, float *inter0, float *inter1,
+                        const int *gate)
 {
     constexpr int P = KickCube<N>::P;
     const size_t smem = (size_t)N * N * P * sizeof(float);
     const int threads = KickCube<N>::NT;
     long long grid = 0;
     cudaError_t e;
-    if (nsweeps == 6 && first_axis == 0 && !inter0 && !inter1) {
+    if (nsweeps == 6 && first_axis == 0 && !inter0 && !inter1 && !gate) {
         e = kick_grid(c, k_kick6<N>, threads, smem, grid);
         if (e != cudaSuccess) return e;
         k_kick6<N><<<(unsigned)grid, threads, smem, c->stream>>>(f, ca, cb, c->np, &c->sc->lost,
@@ -689,7 +700,7 @@ cudaError_t kick_fast_n(vp_ctx *c, float *f, const LineCoef<float> *ca, const Li
     e = kick_grid(c, k_kick_fast<N>, threads, smem, grid);
     if (e != cudaSuccess) return e;
     k_kick_fast<N><<<(unsigned)grid, threads, smem, c->stream>>>(
-        f, ca, cb, nsweeps, first_axis, c->np, &c->sc->lost, fo ? fo : f, inter0, inter1);
+        f, ca, cb, nsweeps, first_axis, c->np, &c->sc->lost, fo ? fo : f, inter0, inter1, gate);
     return cudaGetLastError();
 }
 
@@ -788,14 +799,14 @@ int vp_rho_fuse_ok(const vp_ctx *c)
 }
 
 cudaError_t launch_kick_fast(vp_ctx *c, void *f, const void *ca, const void *cb, int nsweeps,
-                             int first_axis, void *fo, void *inter0, void *inter1)
+                             int first_axis, void *fo, void *inter0, void *inter1, const int *gate)
 {
     if (c->nv[0] == 32)
         return kick_fast_n<32>(c, (float *)f, (const LineCoef<float> *)ca,
                                (const LineCoef<float> *)cb, nsweeps, first_axis, (float *)fo,
-                               (float *)inter0, (float *)inter1);
+                               (float *)inter0, (float *)inter1, gate);
     return kick_fast_n<16>(c, (float *)f, (const LineCoef<float> *)ca, (const LineCoef<float> *)cb,
-                           nsweeps, first_axis, (float *)fo, (float *)inter0, (float *)inter1);
+                           nsweeps, first_axis, (float *)fo, (float *)inter0, (float *)inter1, gate);
 }
 
 cudaError_t launch_drift_fast(vp_ctx *c, void *f, int axis, const void *coef, double *rho_part,
@@ -828,11 +839,13 @@ int vp_drift_yz_ok(const vp_ctx *c)
     return c->nv[2] % vc == 0 && c->n[0] <= 65535 && c->nvc / vc <= 0x7fffffffLL;
 }
 
-cudaError_t launch_drift_yz(vp_ctx *c, const void *f, const void *coef, void *fo)
+cudaError_t launch_drift_yz(vp_ctx *c, const void *f, const void *coef, void *fo, void *fz)
 {
     if (c->n[1] == 32)
-        return drift_yz_n<32>(c, (const float *)f, (const LineCoef<float> *)coef, (float *)fo);
-    return drift_yz_n<16>(c, (const float *)f, (const LineCoef<float> *)coef, (float *)fo);
+        return drift_yz_n<32>(c, (const float *)f, (const LineCoef<float> *)coef, (float *)fo,
+                              (float *)fz);
+    return drift_yz_n<16>(c, (const float *)f, (const LineCoef<float> *)coef, (float *)fo,
+                          (float *)fz);
 }
 
 cudaError_t launch_rho_finish(vp_ctx *c, const double *part, int nparts, double *rho)

@@ -133,15 +133,18 @@ def test_adjoint_step_matches_oracle(bc):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("G", [20.0, 200.0])
-def test_adjoint_step_fp32_register_kernels_match_oracle(G):
-    """FP32 adjoint step on a grid served by the packed kernels (x lines of
-    16 with the density broadcast added on load, 16^3 velocity cubes)
-    against the FP64 oracle's adjoint step.  With the large G the kicks
-    shift by whole cells: the replay's shifted-cube path and the adjoint's
-    fix-up pass."""
-    w = I.small_maxwell(n=(16, 2, 2), nv=(16, 16, 16), dtype="f32", amp=0.2, G=G)
-    w = w.replace(dt_fixed=0.01, box_lo=(-0.5, -0.05, -0.05), box_hi=(0.5, 0.05, 0.05))
+@pytest.mark.parametrize("G,n", [(20.0, (16, 2, 2)), (200.0, (16, 2, 2)), (20.0, (2, 16, 16))])
+def test_adjoint_step_fp32_register_kernels_match_oracle(G, n):
+    """FP32 adjoint step on grids served by the packed kernels against the
+    FP64 oracle's adjoint step: x lines of 16 with the density broadcast
+    added on load, 16^3 velocity cubes (vz input recomputed); y and z lines
+    of 16 (the replay's fused z + y drift keeping the z output, the z
+    adjoint's warp-uniform direction map, pairs straddling v_z = 0).  With
+    the large G the kicks shift by whole cells: the replay's shifted-cube
+    path and the adjoint's fix-up pass."""
+    w = I.small_maxwell(n=n, nv=(16, 16, 16), dtype="f32", amp=0.2, G=G)
+    half = tuple(0.5 if m == 16 else 0.05 for m in n)
+    w = w.replace(dt_fixed=0.01, box_lo=tuple(-h for h in half), box_hi=half)
     grid = O.Grid.of(w)
     rng = np.random.default_rng(4)
     f0 = (I.initial_condition(w, np.float64) * (1 + 0.2 * rng.random(w.shape))).astype(np.float32)
@@ -150,7 +153,9 @@ def test_adjoint_step_fp32_register_kernels_match_oracle(G):
     lam_f = torch.from_numpy(rng.normal(size=w.shape).astype(np.float32)).to(DEV)
     lam_g = torch.from_numpy(rng.normal(size=(3,) + w.n)).to(DEV)
     lf0, lg0 = lam_f.cpu().numpy().astype(np.float64), lam_g.cpu().numpy()
+    m_out = sim.energy()["M_out"]
     sim.adjoint_step(torch.from_numpy(f0).to(DEV), g0, lam_f, lam_g)
+    assert sim.energy()["M_out"] == m_out        # the replay's outflow is not the run's
     f64 = f0.astype(np.float64)
     osim = O.Simulation(f64, grid, O.Params.of(w))
     rf, rg = O.adjoint_step(osim, f64, osim.g, lf0, lg0)
