@@ -461,6 +461,7 @@ __global__ void __launch_bounds__(128) k_adjoint_fast(AdjArgs<T> A, LineGeom g, 
 int vp_adjoint_fast_ok(const vp_ctx *c, int axis)
 {
     const int n = axis < 3 ? c->n[axis] : c->nv[axis - 3];
+    if (axis >= 3 && c->np > 65535) return 0;     // one grid row per cube
     if (c->isdouble) return n == 16;
     return n == 16 || n == 32 || n == 48 || n == 64;
 }

@@ -364,14 +364,15 @@ int vp_init(const vp_config *cfg, void *f_dev, void *cuda_stream, vp_ctx **out)
     };
     // size limits of the kernels
     {
-        const size_t cube = (size_t)c->nv[0] * c->nv[1] * (c->nv[2] | 1) * c->esize;
-        if (cube > 220 * 1024) return fail(VP_ERR_UNSUPPORTED);
+        // drift tiles N_l x C and per-axis kick tiles N^v_l x (C + 1); cubes
+        // above the shared-memory size are kicked one axis per pass
         for (int a = 0; a < 3; ++a) {
             const size_t tile = (size_t)c->n[a] * (c->isdouble ? 128 : 256) * c->esize;
-            if (tile > 220 * 1024) return fail(VP_ERR_UNSUPPORTED);
+            const size_t ktile = (size_t)c->nv[a] * (c->isdouble ? 129 : 257) * c->esize;
+            if (tile > 220 * 1024 || ktile > 220 * 1024) return fail(VP_ERR_UNSUPPORTED);
         }
         if (c->nvc > 0x7fffffffLL || c->np / c->n[0] > 65535 || c->np / c->n[1] > 65535 ||
-            c->np / c->n[2] > 65535)
+            c->np / c->n[2] > 65535 || c->np > 0x7fffffffLL)
             return fail(VP_ERR_UNSUPPORTED);
     }
     if (c->isolated) {

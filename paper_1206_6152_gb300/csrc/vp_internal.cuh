@@ -131,6 +131,11 @@ int vp_kick_fast_ok(const vp_ctx *c);
 int vp_drift_fast_ok(const vp_ctx *c, int axis);
 int vp_rho_fuse_ok(const vp_ctx *c);
 int vp_rho_parts(vp_ctx *c);
+// FP32 cubes of edge 48: kick sweeps one pass per vx sweep and per run of
+// consecutive vy / vz sweeps, lines in registers
+int vp_kick_big_ok(const vp_ctx *c);
+cudaError_t launch_kick_big(vp_ctx *c, void *f, const void *ca, const void *cb, int nsweeps,
+                            int first_axis);
 // fused z then y drift of the whole grid (in place when fo == f); fz, if not
 // null, also receives the z sweep's output (fz != f)
 int vp_drift_yz_ok(const vp_ctx *c);

@@ -82,6 +82,94 @@ __device__ T kick_line(T *L, int st, int n, const LineCoef<T> cf)
 }
 
 // ---------------------------------------------------------------------------
+// one kick sweep along velocity axis va for cubes too large for shared
+// memory: each CTA stages C lines of one cube in a tile [n][C + 1] (line t
+// in column t), lines along vx or vy with one coalesced load per cell
+// index, rows (vz) with a cooperative load of the contiguous rows
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_kick_axis(T *__restrict__ f,
+                                                  const LineCoef<T> *__restrict__ coef, int va,
+                                                  int nx, int ny, int nz, long long np,
+                                                  double *lost_out)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *tile = reinterpret_cast<T *>(smem_raw);
+    __shared__ Acc<double> red[32];
+    const int C = blockDim.x, CP = C + 1, t = threadIdx.x;
+    const int n = va == 0 ? nx : (va == 1 ? ny : nz);
+    const int lines = nx * ny * nz / n;
+    const long long cell = blockIdx.x;
+    T *g = f + cell * (long long)nx * ny * nz;
+    const int l0 = blockIdx.y * C;
+    const int cnt = lines - l0 < C ? lines - l0 : C;
+    const int l = l0 + t;
+    const bool active = t < cnt;
+    long long off = 0, stride = 1;
+    if (va == 0) { off = l; stride = (long long)ny * nz; }            // l = j nz + k
+    else if (va == 1) { off = (long long)(l / nz) * ny * nz + l % nz; stride = nz; }
+    if (va < 2) {
+        if (active)
+            for (int j = 0; j < n; ++j) tile[j * CP + t] = g[off + j * stride];
+    } else {
+        for (int e = t; e < cnt * nz; e += C) tile[(e % nz) * CP + e / nz] = g[(long long)l0 * nz + e];
+        __syncthreads();
+    }
+    T lost = T(0);
+    if (active) lost = kick_line(tile + t, CP, n, coef[cell * 3 + va]);
+    if (va < 2) {
+        if (active)
+            for (int j = 0; j < n; ++j) g[off + j * stride] = tile[j * CP + t];
+    } else {
+        __syncthreads();
+        for (int e = t; e < cnt * nz; e += C) g[(long long)l0 * nz + e] = tile[(e % nz) * CP + e / nz];
+    }
+    Acc<double> a;
+    a.add((double)lost);
+    a = block_merge(a, red);
+    if (t == 0 && a.value() != 0.0) atomicAdd(lost_out, a.value());
+}
+
+// ---------------------------------------------------------------------------
+// consecutive kick sweeps along vy and vz (in the order given) for cubes too
+// large for shared memory: both are local to one vx plane, so one CTA stages
+// one plane [ny][nz + 1] (odd pitch: rows and columns conflict-free), runs
+// the sweeps (one line per thread) and writes the plane back
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_kick_plane(T *__restrict__ f,
+                                                   const LineCoef<T> *__restrict__ c0, int a0,
+                                                   const LineCoef<T> *__restrict__ c1, int a1,
+                                                   int nsw, int nx, int ny, int nz,
+                                                   double *lost_out)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *tile = reinterpret_cast<T *>(smem_raw);
+    __shared__ Acc<double> red[32];
+    const int P = nz + 1, t = threadIdx.x;
+    const long long cell = blockIdx.x;
+    T *g = f + (cell * nx + blockIdx.y) * (long long)ny * nz;
+    for (int e = t; e < ny * nz; e += blockDim.x) tile[(e / nz) * P + e % nz] = g[e];
+    __syncthreads();
+    T lost = T(0);
+    for (int sw = 0; sw < nsw; ++sw) {
+        const int va = sw ? a1 : a0;
+        const LineCoef<T> cf = (sw ? c1 : c0)[cell * 3 + va];
+        if (va == 1) {
+            for (int k = t; k < nz; k += blockDim.x) lost += kick_line(tile + k, P, ny, cf);
+        } else {
+            for (int j = t; j < ny; j += blockDim.x) lost += kick_line(tile + j * P, 1, nz, cf);
+        }
+        __syncthreads();
+    }
+    for (int e = t; e < ny * nz; e += blockDim.x) g[e] = tile[(e / nz) * P + e % nz];
+    Acc<double> a;
+    a.add((double)lost);
+    a = block_merge(a, red);
+    if (t == 0 && a.value() != 0.0) atomicAdd(lost_out, a.value());
+}
+
+// ---------------------------------------------------------------------------
 // kick: NX, NY, NZ compile-time cube edges (0 = runtime)
 // ---------------------------------------------------------------------------
 template <typename T, int NX, int NY, int NZ>
@@ -285,7 +373,24 @@ __global__ void __launch_bounds__(256) k_density(const T *__restrict__ f, long l
     for (long long cell = blockIdx.x; cell < np; cell += gridDim.x) {
         const T *q = f + cell * (long long)nvc;
         Acc<T> a;
-        for (int e = threadIdx.x; e < nvc; e += blockDim.x) a.add(q[e]);
+        if (sizeof(T) == 4 && (nvc & 3) == 0) {
+            // four independent compensated sums (one per float4 lane) for
+            // memory-level parallelism, merged at the end
+            Acc<T> b, c2, d;
+            const float4 *q4 = reinterpret_cast<const float4 *>(q);
+            for (int e = threadIdx.x; e < nvc / 4; e += blockDim.x) {
+                const float4 v = q4[e];
+                a.add((T)v.x);
+                b.add((T)v.y);
+                c2.add((T)v.z);
+                d.add((T)v.w);
+            }
+            a.merge(b);
+            c2.merge(d);
+            a.merge(c2);
+        } else {
+            for (int e = threadIdx.x; e < nvc; e += blockDim.x) a.add(q[e]);
+        }
         a = block_merge(a, red);
         if (threadIdx.x == 0) rho[cell] = a.value() * dvol;
         __syncthreads();
@@ -362,10 +467,62 @@ cudaError_t launch_kick_t(vp_ctx *c, T *f, const LineCoef<T> *ca, const LineCoef
     return cudaGetLastError();
 }
 
+// cube in shared memory (odd row pitch) for the whole-cube kernel
+size_t kick_cube_bytes(const vp_ctx *c)
+{
+    return (size_t)c->nv[0] * c->nv[1] * (c->nv[2] | 1) * c->esize;
+}
+
+template <typename T>
+cudaError_t launch_kick_axes(vp_ctx *c, T *f, const LineCoef<T> *ca, const LineCoef<T> *cb,
+                             int nsweeps, int first_axis)
+{
+    const int C = sizeof(T) == 8 ? 128 : 256;
+    cudaError_t e;
+    for (int sw = 0; sw < nsweeps;) {
+        const int va = (first_axis + sw) % 3;
+        const LineCoef<T> *cf = sw < 3 ? ca : cb;
+        if (va > 0) {
+            // a run of sweeps local to vx planes: this one and, if it is
+            // along the other of vy / vz, the next
+            int nsw = 1;
+            const int vb = (first_axis + sw + 1) % 3;
+            if (sw + 1 < nsweeps && vb > 0) nsw = 2;
+            const size_t smem = (size_t)c->nv[1] * (c->nv[2] + 1) * sizeof(T);
+            if ((e = cudaFuncSetAttribute(k_kick_plane<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem)) != cudaSuccess)
+                return e;
+            int threads = ((c->nv[1] > c->nv[2] ? c->nv[1] : c->nv[2]) + 31) / 32 * 32;
+            if (threads > 256) threads = 256;
+            const dim3 grid((unsigned)c->np, (unsigned)c->nv[0]);
+            k_kick_plane<T><<<grid, threads, smem, c->stream>>>(
+                f, cf, va, (sw + 1 < 3 ? ca : cb), vb, nsw, c->nv[0], c->nv[1], c->nv[2],
+                &c->sc->lost);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            sw += nsw;
+            continue;
+        }
+        const int n = c->nv[va];
+        const long long lines = c->nvc / n;
+        const size_t smem = (size_t)n * (C + 1) * sizeof(T);
+        if ((e = cudaFuncSetAttribute(k_kick_axis<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem)) != cudaSuccess)
+            return e;
+        const dim3 grid((unsigned)c->np, (unsigned)((lines + C - 1) / C));
+        k_kick_axis<T><<<grid, C, smem, c->stream>>>(f, cf, va, c->nv[0], c->nv[1], c->nv[2],
+                                                     c->np, &c->sc->lost);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        ++sw;
+    }
+    return cudaSuccess;
+}
+
 template <typename T>
 cudaError_t launch_kick_dispatch(vp_ctx *c, T *f, const LineCoef<T> *ca, const LineCoef<T> *cb,
                                  int nsweeps, int first_axis)
 {
+    if (kick_cube_bytes(c) > 220 * 1024)
+        return launch_kick_axes<T>(c, f, ca, cb, nsweeps, first_axis);
     const int nx = c->nv[0], ny = c->nv[1], nz = c->nv[2];
     if (nx == ny && ny == nz) {
         if (nx == 16) return launch_kick_t<T, 16, 16, 16>(c, f, ca, cb, nsweeps, first_axis);
@@ -483,6 +640,7 @@ cudaError_t launch_kick(vp_ctx *c, void *f, const void *coef_a, const void *coef
                         int first_axis)
 {
     if (vp_kick_fast_ok(c)) return launch_kick_fast(c, f, coef_a, coef_b, nsweeps, first_axis);
+    if (vp_kick_big_ok(c)) return launch_kick_big(c, f, coef_a, coef_b, nsweeps, first_axis);
     if (c->isdouble)
         return launch_kick_dispatch<double>(c, (double *)f, (const LineCoef<double> *)coef_a,
                                             (const LineCoef<double> *)coef_b, nsweeps,

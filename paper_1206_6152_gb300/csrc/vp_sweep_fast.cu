@@ -419,6 +419,115 @@ __global__ void __launch_bounds__(KickCube<N>::NT) k_kick6(float *__restrict__ f
 }
 
 // ---------------------------------------------------------------------------
+// kick sweeps for FP32 cubes too large for shared memory (edge N = 48):
+//  * k_kick_vx_big: lines along vx, two per thread (adjacent vz, packed),
+//    straight from global memory (a warp reads two 192-byte row pieces);
+//  * k_kick_plane_big: one or two consecutive sweeps along vy / vz, which
+//    are local to a vx plane: each CTA stages four planes [N][N + 1] (odd
+//    pitch: rows and columns conflict-free) and sweeps one line per thread
+//    in registers.
+// A line with a whole-cell shift takes the generic in-place routine.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(128) k_kick_vx_big(float *__restrict__ f,
+                                                    const LineCoef<float> *__restrict__ coef,
+                                                    long long np, double *lost_out)
+{
+    __shared__ Acc<double> red[32];
+    constexpr int H = N / 2;
+    const int t = threadIdx.x;
+    const long long cell = blockIdx.x;
+    const int u = blockIdx.y * blockDim.x + t;            // pair index (j, k)
+    float lost = 0.f;
+    if (u < N * H) {
+        const LineCoef<float> cf = coef[cell * 3];
+        float *g = f + cell * (long long)N * N * N + (u / H) * N + 2 * (u % H);
+        if ((cf.code >> 1) == 0) {
+            float2 x[N];
+#pragma unroll
+            for (int i = 0; i < N; ++i) x[i] = *reinterpret_cast<const float2 *>(g + i * N * N);
+            lost += sweep_pairs<N>(x, cf);
+#pragma unroll
+            for (int i = 0; i < N; ++i) *reinterpret_cast<float2 *>(g + i * N * N) = x[i];
+        } else {
+            lost += kick_line_shifted(g, N * N, N, cf);
+            lost += kick_line_shifted(g + 1, N * N, N, cf);
+        }
+    }
+    Acc<double> a;
+    a.add((double)lost);
+    a = block_merge(a, red);
+    if (t == 0 && a.value() != 0.0) atomicAdd(lost_out, a.value());
+}
+
+template <int N>
+struct PlaneBig {
+    static constexpr int P = N + 1, PPC = 4, NT = PPC * N;   // planes per CTA, threads
+    static constexpr size_t SMEM = (size_t)PPC * N * P * sizeof(float);
+};
+
+template <int N>
+__global__ void __launch_bounds__(PlaneBig<N>::NT, 3) k_kick_plane_big(
+    float *__restrict__ f, const LineCoef<float> *__restrict__ c0, int a0,
+    const LineCoef<float> *__restrict__ c1, int a1, int nsw, double *lost_out)
+{
+    constexpr int P = PlaneBig<N>::P, PPC = PlaneBig<N>::PPC, NT = PlaneBig<N>::NT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *tile = reinterpret_cast<float *>(smem_raw);
+    __shared__ Acc<double> red[32];
+    const int t = threadIdx.x, pl = t / N, m = t % N;
+    const long long cell = blockIdx.x;
+    const int i0 = blockIdx.y * PPC;                      // first plane of the CTA
+    float *g = f + (cell * N + i0) * (long long)N * N;   // PPC contiguous planes
+    // thread t moves column t % N of rows t / N, t / N + NT / N, ... (the
+    // PPC planes are PPC * N contiguous rows)
+    constexpr int RS = NT / N, NR = PPC * N / RS;         // rows per step, rows per thread
+    {
+        float v[NR];                                      // all loads in flight at once
+        const float *gp = g + (t / N) * N + m;
+#pragma unroll
+        for (int i = 0; i < NR; ++i) v[i] = gp[i * RS * N];
+        float *tp = tile + (t / N) * P + m;
+#pragma unroll
+        for (int i = 0; i < NR; ++i) tp[i * RS * P] = v[i];
+    }
+    __syncthreads();
+    float lost = 0.f;
+    float *pt = tile + pl * N * P;
+    for (int sw = 0; sw < nsw; ++sw) {
+        const int va = sw ? a1 : a0;
+        const LineCoef<float> cf = (sw ? c1 : c0)[cell * 3 + va];
+        float *L = va == 1 ? pt + m : pt + m * P;          // column m (vy) or row m (vz)
+        const int st = va == 1 ? P : 1;
+        if ((cf.code >> 1) == 0) {
+            float x[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) x[j] = L[j * st];
+            const LineW<float> w = weights_one<float>(cf, line_max(x));
+            lost += update_line<float, N, false>(x, w, cf.code & 1);
+#pragma unroll
+            for (int j = 0; j < N; ++j) L[j * st] = x[j];
+        } else {
+            lost += kick_line_shifted(L, st, N, cf);
+        }
+        __syncthreads();
+    }
+    {
+        float v[NR];
+        const float *tp = tile + (t / N) * P + m;
+#pragma unroll
+        for (int i = 0; i < NR; ++i) v[i] = tp[i * RS * P];
+        float *gp = g + (t / N) * N + m;
+#pragma unroll
+        for (int i = 0; i < NR; ++i) gp[i * RS * N] = v[i];
+    }
+    Acc<double> a;
+    a.add((double)lost);
+    a = block_merge(a, red);
+    if (t == 0 && a.value() != 0.0) atomicAdd(lost_out, a.value());
+}
+
+// ---------------------------------------------------------------------------
 // drift: lines along a spatial axis, held in registers
 // ---------------------------------------------------------------------------
 struct DriftGeom {
@@ -846,6 +955,47 @@ cudaError_t launch_drift_yz(vp_ctx *c, const void *f, const void *coef, void *fo
                               (float *)fz);
     return drift_yz_n<16>(c, (const float *)f, (const LineCoef<float> *)coef, (float *)fo,
                           (float *)fz);
+}
+
+// FP32 cubes of edge 48 (too large for shared memory): sweeps one pass per
+// vx sweep, one pass per run of consecutive vy / vz sweeps
+int vp_kick_big_ok(const vp_ctx *c)
+{
+    const int n = c->nv[0];
+    return !c->isdouble && n == c->nv[1] && n == c->nv[2] && n == 48;
+}
+
+cudaError_t launch_kick_big(vp_ctx *c, void *f_, const void *ca_, const void *cb_, int nsweeps,
+                            int first_axis)
+{
+    constexpr int N = 48;
+    float *f = (float *)f_;
+    const LineCoef<float> *ca = (const LineCoef<float> *)ca_, *cb = (const LineCoef<float> *)cb_;
+    cudaError_t e;
+    for (int sw = 0; sw < nsweeps;) {
+        const int va = (first_axis + sw) % 3;
+        const LineCoef<float> *cf = sw < 3 ? ca : cb;
+        if (va == 0) {
+            const dim3 grid((unsigned)c->np, (unsigned)((N * N / 2 + 127) / 128));
+            k_kick_vx_big<N><<<grid, 128, 0, c->stream>>>(f, cf, c->np, &c->sc->lost);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            ++sw;
+            continue;
+        }
+        int nsw = 1;
+        const int vb = (first_axis + sw + 1) % 3;
+        if (sw + 1 < nsweeps && vb > 0) nsw = 2;
+        typedef PlaneBig<N> PB;
+        if ((e = cudaFuncSetAttribute(k_kick_plane_big<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)PB::SMEM)) != cudaSuccess)
+            return e;
+        const dim3 grid((unsigned)c->np, (unsigned)(N / PB::PPC));
+        k_kick_plane_big<N><<<grid, PB::NT, PB::SMEM, c->stream>>>(f, cf, va, sw + 1 < 3 ? ca : cb, vb,
+                                                                   nsw, &c->sc->lost);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        sw += nsw;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_rho_finish(vp_ctx *c, const double *part, int nparts, double *rho)

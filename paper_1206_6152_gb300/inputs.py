@@ -209,8 +209,15 @@ def jeans_slab_x() -> Workload:
     return jeans_c2().replace(name="jeans_slab_x_f32", n=(32, 8, 8))
 
 
+def jeans48_slab() -> Workload:
+    """8^3 spatial cells of the 48^3 x 48^3 box (226 MB of FP32 f, above L2):
+    the 48^3-cube kick kernels for hardware-counter captures."""
+    return large_c5().replace(name="jeans48_slab_f32", n=(8, 8, 8))
+
+
 WORKLOADS = {
     "jeans16x32_f32": jeans_profile,
+    "jeans48_slab_f32": jeans48_slab,
     "jeans_slab_yz_f32": jeans_slab_yz,
     "jeans_slab_x_f32": jeans_slab_x,
     "landau16_f64": landau_c1,
@@ -259,16 +266,23 @@ def maxwellian_v(w: Workload) -> np.ndarray:
     return e * (2 * math.pi * s2) ** -1.5
 
 
+def factors(w: Workload, amplitudes=None):
+    """The Maxwellian initial condition as an outer product f = rho(x) M(v):
+    (rho on the spatial centres, flat; M on the velocity centres, flat), both
+    FP64.  The product of the two, rounded once, is initial_condition()."""
+    rho_x = w.rho_bar * (1.0 + density_contrast(w, amplitudes))
+    return rho_x.reshape(-1), maxwellian_v(w).reshape(-1)
+
+
 def initial_condition(w: Workload, dtype=None, amplitudes=None) -> np.ndarray:
     """f(x, v, t=0) on the cell centres, C order [x][y][z][vx][vy][vz].
     Computed in FP64 and rounded once to the storage type."""
     dt = np.dtype(dtype or ("float32" if w.dtype == "f32" else "float64"))
     if w.ic == "king":
         return king_initial_condition(w, dt)
-    rho_x = w.rho_bar * (1.0 + density_contrast(w, amplitudes))
-    mv = maxwellian_v(w).reshape(-1)
+    rho_x, mv = factors(w, amplitudes)
     out = np.empty((int(np.prod(w.n)), mv.size), dtype=dt)
-    flat = rho_x.reshape(-1)
+    flat = rho_x
     step = max(1, (1 << 24) // mv.size)
     for s in range(0, flat.size, step):
         e = min(flat.size, s + step)

@@ -49,6 +49,8 @@ SMALL = [
     # velocity counts, a 32-cell vz axis for the warp-uniform z mapping)
     dict(n=(16, 32, 16), nv=(4, 6, 10)),
     dict(n=(16, 16, 16), nv=(2, 4, 32)),
+    # velocity cubes above shared memory (48^3: one sweep per pass)
+    dict(n=(2, 1, 2), nv=(48, 48, 48)),
 ]
 
 
@@ -306,3 +308,91 @@ def test_jeans_32_full_size_two_steps():
     assert diff.max() <= 1e-5 * ref.f.max()
     assert got.min() >= 0.0
     assert abs(e["M"] + e["M_out"] - M0) <= 1e-7 * M0
+
+
+def device_initial_condition(w, dtype=torch.float32):
+    """initial_condition(w) built on the GPU from its two FP64 factors (the
+    same products, rounded once)."""
+    rho, mv = I.factors(w)
+    r = torch.from_numpy(rho).to(DEV)
+    m = torch.from_numpy(mv).to(DEV)
+    f = torch.empty((r.numel(), m.numel()), dtype=dtype, device=DEV)
+    step = max(1, (1 << 26) // m.numel())
+    for s in range(0, r.numel(), step):
+        f[s:s + step] = (r[s:s + step, None] * m[None, :]).to(dtype)
+    return f.reshape(w.shape)
+
+
+@pytest.mark.gpu
+def test_split_steps_48_cubes_match_oracle():
+    """FP32 split steps with 48^3 velocity cubes (kicked one axis per pass)
+    and 4^3 positions against the oracle."""
+    w = I.large_c5().replace(n=(4, 4, 4), box_lo=(-0.5,) * 3, box_hi=(0.5,) * 3)
+    f0 = I.initial_condition(w)
+    sim, f = gpu_sim(w, f0)
+    t = sim.step(2, sync=True)
+    got = f.cpu().numpy().astype(np.float64)
+    ref = O.Simulation(f0.astype(np.float64), O.Grid.of(w), O.Params.of(w))
+    ref.step(2)
+    assert abs(t - ref.t) <= 1e-6 * ref.t
+    assert rel_l1(got, ref.f) <= 4e-6
+    assert got.min() >= 0.0
+    sim.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.slow
+def test_jeans48_full_size_sweeps_and_steps():
+    """The 48^3 x 48^3 FP32 box (49 GB of f) in the benchmark's launch
+    configuration: one kick sweep per velocity axis and one drift sweep per
+    position axis checked on sampled cubes and lines against the oracle, then
+    two split steps: mass, positivity and time."""
+    w = I.large_c5()
+    grid = O.Grid.of(w)
+    f = device_initial_condition(w)
+    from paper_1206_6152_gb300.vlasov import VlasovPoisson, config_of
+    sim = VlasovPoisson(config_of(w, torch.float32), f)
+    rng = np.random.default_rng(5)
+    np_ = int(np.prod(w.n))
+    g = sim.field()[2].cpu().numpy().reshape(3, -1)
+    cells = rng.choice(np_, 6, replace=False)
+    tau = 0.3 * float(grid.dv[0]) / max(np.abs(g).max(), 1e-300)    # |alpha| <= 0.3
+    fv = f.view(np_, -1)
+    for va in range(3):
+        before = fv[cells].cpu().numpy().astype(np.float64).reshape((len(cells), 1, 1) + w.nv)
+        sim.sweep(3 + va, tau)
+        after = fv[cells].cpu().numpy().astype(np.float64).reshape(before.shape)
+        O.sweep(before, 3 + va, g[va][cells].reshape(len(cells), 1, 1), tau, grid.dv[va], False)
+        assert np.abs(after - before).max() <= 2e-6 * before.max(), va
+    # drift: lines along each position axis at sampled velocity cells
+    f6 = f.view(w.shape)
+    tau_d = 0.4 * float(grid.dx[0]) / 5.0
+    vsel = [(int(a), int(b), int(c)) for a, b, c in rng.integers(0, 48, size=(4, 3))]
+    yz = [(int(a), int(b)) for a, b in rng.integers(0, 48, size=(2, 2))]
+    def lines(axis):
+        out = []
+        for (p, q) in yz:
+            for v in vsel:
+                if axis == 0: out.append(f6[:, p, q, v[0], v[1], v[2]])
+                elif axis == 1: out.append(f6[p, :, q, v[0], v[1], v[2]])
+                else: out.append(f6[p, q, :, v[0], v[1], v[2]])
+        return [l.cpu().numpy().astype(np.float64) for l in out]
+    for axis in range(3):
+        before = lines(axis)
+        sim.sweep(axis, tau_d)
+        after = lines(axis)
+        k = 0
+        for (p, q) in yz:
+            for v in vsel:
+                alpha = grid.vc(axis)[v[axis]] * tau_d / grid.dx[axis]
+                ref = O.pfc_line(before[k], alpha, True)
+                assert np.abs(after[k] - ref).max() <= 2e-6 * max(before[k].max(), 1e-300), axis
+                k += 1
+    sim.refresh_field()
+    M0 = sim.energy()["M"]
+    t = sim.step(2, sync=True)
+    e = sim.energy()
+    assert abs(e["M"] - M0) <= 1e-6 * M0
+    assert float(f.min()) >= 0.0
+    assert t > 0
+    sim.close()
