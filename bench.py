@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--profile-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--adjoint-steps", type=int, default=3)
+    p.add_argument("--adjoint-workload", default="jeans32_modes3")
     p.add_argument("--cpu-sample", type=float, default=1.0 / 64)
     return p.parse_args()
 
@@ -386,8 +387,11 @@ def time_adjoint(args, dev, stream):
     import torch
     from paper_1206_6152_gb300 import inputs as I
     from paper_1206_6152_gb300.vlasov import VlasovPoisson, config_of
-    w = I.adjoint_c4()
-    f = torch.from_numpy(I.initial_condition(w)).to(dev)
+    w = I.WORKLOADS[args.adjoint_workload]()
+    if w.cells * (4 if w.dtype == "f32" else 8) > HOST_F_LIMIT:
+        f = device_initial_condition(w, dev, torch.float32 if w.dtype == "f32" else torch.float64)
+    else:
+        f = torch.from_numpy(I.initial_condition(w)).to(dev)
     sim = VlasovPoisson(config_of(w), f, stream)
     k = args.adjoint_steps
     sim.step(3)
@@ -414,8 +418,9 @@ def time_adjoint(args, dev, stream):
     sim.close()
     return {"workload": w.name, "forward_ms_per_step": round(fwd, 3),
             "adjoint_ms_per_step": round(adj, 3), "ratio": round(adj / fwd, 3),
-            "note": "adjoint step = replay of its forward step (9 sweeps, kept) + 9 adjoint sweeps "
-                    "+ field adjoint; segment recompute of the checkpoints not included"}
+            "note": "adjoint step = replay of its forward step keeping the sweep inputs it cannot "
+                    "recompute locally + 9 adjoint sweeps + field adjoint; the recompute of the "
+                    "step-start states from the checkpoints is not included"}
 
 
 def run_reference(args, ranks: Ranks):

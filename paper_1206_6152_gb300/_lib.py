@@ -21,6 +21,7 @@ EXPORTS = (
     "vp_moments", "vp_get_field", "vp_set_accel", "vp_energy", "vp_time", "vp_step_host",
     "vp_adjoint_step", "vp_field_adjoint", "vp_functional", "vp_destroy", "vp_error_string",
     "vp_profile_step", "vp_stats", "vp_sweep_adjoint", "vp_moments_noalloc",
+    "vp_set_adjoint_states",
 )
 PROFILE_SLOTS = 8
 PROFILE_NAMES = ("kick6", "drift_z", "drift_y", "drift_x", "density", "field", "tables", "step")
@@ -79,6 +80,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "vp_time": (i, [vp, dp, dp]),
             "vp_step_host": (i, [vp, vp, vp, i, dp, dp]),
             "vp_adjoint_step": (i, [vp, vp, vp, vp, vp]),
+            "vp_set_adjoint_states": (i, [vp, i]),
             "vp_field_adjoint": (i, [vp, vp, vp]),
             "vp_sweep_adjoint": (i, [vp, i, d, vp, vp, vp]),
             "vp_moments_noalloc": (i, [vp, i, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),

@@ -402,7 +402,10 @@ __global__ void __launch_bounds__(128) k_adjoint_fast(AdjArgs<T> A, LineGeom g, 
 {
     __shared__ double red[32];
     const int t = threadIdx.x;
-    const long long w = (long long)blockIdx.x * blockDim.x + t;
+    // velocity axes: blockIdx.x is the cube (any number of cubes), blockIdx.y
+    // the chunk of its lines
+    const bool vel = g.axis >= 3;
+    const long long w = (long long)(vel ? blockIdx.y : blockIdx.x) * blockDim.x + t;
     bool active = w < g.nlines_inner;
     long long base = 0;
     LineCoef<T> cf;
@@ -412,7 +415,7 @@ __global__ void __launch_bounds__(128) k_adjoint_fast(AdjArgs<T> A, LineGeom g, 
         base = cell0 * g.nvc + w;
         if (active) cf = A.coef[(int)((w / A.va_stride) % A.va_n)];
     } else {
-        const long long cell = blockIdx.y;
+        const long long cell = blockIdx.x;
         const long long voff = (w / g.wdiv) * g.wmul_hi + (w % g.wdiv) * g.wmul_lo;
         base = cell * g.nvc + voff;
         cf = A.coef[cell * 3 + (g.axis - 3)];
@@ -454,22 +457,23 @@ __global__ void __launch_bounds__(128) k_adjoint_fast(AdjArgs<T> A, LineGeom g, 
     }
     if (A.lam_g) {
         da = block_sum(da, red);
-        if (t == 0 && da != 0.0) atomicAdd(A.lam_g + blockIdx.y, da * A.dalpha_scale);
+        if (t == 0 && da != 0.0) atomicAdd(A.lam_g + blockIdx.x, da * A.dalpha_scale);
     }
 }
 
 int vp_adjoint_fast_ok(const vp_ctx *c, int axis)
 {
     const int n = axis < 3 ? c->n[axis] : c->nv[axis - 3];
-    if (axis >= 3 && c->np > 65535) return 0;     // one grid row per cube
     if (c->isdouble) return n == 16;
     return n == 16 || n == 32 || n == 48 || n == 64;
 }
 
 template <typename T, int N>
 cudaError_t adjoint_fast_n(vp_ctx *c, const AdjArgs<T> &A, const LineGeom &g, dim3 grid)
+// grid: (line chunks, outer index or cube)
 {
     const bool rows = g.stride == 1 && sizeof(T) == 4 && (c->nvc % 4) == 0;
+    if (g.axis >= 3) grid = dim3(grid.y, grid.x);        // (cube, chunk)
     if (A.periodic) {
         if (rows) k_adjoint_fast<T, N, true, true><<<grid, 128, 0, c->stream>>>(A, g, c->adj_flag);
         else k_adjoint_fast<T, N, true, false><<<grid, 128, 0, c->stream>>>(A, g, c->adj_flag);
@@ -591,32 +595,52 @@ inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
         if (_r != VP_OK) return _r; \
     } while (0)
 
+void free_adjoint_states(vp_ctx *c)
+{
+    if (!c->adj_states) return;
+    for (int i = 0; i < c->adj_nstates; ++i)
+        if (c->adj_states[i]) cudaFree(c->adj_states[i]);
+    free(c->adj_states);
+    c->adj_states = nullptr;
+    c->adj_nstates = 0;
+}
+
+// n states of f's size; false (nothing kept) if they do not fit
+bool alloc_adjoint_states(vp_ctx *c, int n)
+{
+    const size_t bytes = (size_t)c->ncells * c->esize;
+    c->adj_states = (void **)calloc(n, sizeof(void *));
+    if (!c->adj_states) return false;
+    c->adj_nstates = n;
+    for (int i = 0; i < n; ++i)
+        if (cudaMalloc(&c->adj_states[i], bytes) != cudaSuccess) {
+            cudaGetLastError();
+            free_adjoint_states(c);
+            return false;
+        }
+    return true;
+}
+
 int ensure_adjoint_scratch(vp_ctx *c)
 {
     if (c->adj_states) return VP_OK;
-    if (c->adj_flag) {
-        cudaFree(c->adj_flag);
-        c->adj_flag = nullptr;
-    }
-    const size_t bytes = (size_t)c->ncells * c->esize;
-    c->adj_nstates = 9;
-    c->adj_states = (void **)calloc(9, sizeof(void *));
-    if (!c->adj_states) return VP_ERR_OOM;
-    for (int i = 0; i < 9; ++i)
-        if (cudaMalloc(&c->adj_states[i], bytes) != cudaSuccess) {
+    if (!c->adj_f) {
+        const size_t cs = c->isdouble ? sizeof(LineCoef<double>) : sizeof(LineCoef<float>);
+        if (!c->adj_flag && cudaMalloc((void **)&c->adj_flag, sizeof(int)) != cudaSuccess) {
             cudaGetLastError();
             return VP_ERR_OOM;
         }
-    const size_t cs = c->isdouble ? sizeof(LineCoef<double>) : sizeof(LineCoef<float>);
-    if (cudaMalloc(&c->adj_f, cs * 3 * c->np) != cudaSuccess ||   // K1 table of the replay
-        cudaMalloc((void **)&c->adj_g, sizeof(double) * 3 * c->np) != cudaSuccess ||
-        cudaMalloc((void **)&c->adj_lg, sizeof(double) * 3 * c->np) != cudaSuccess ||
-        cudaMalloc((void **)&c->adj_tmp, sizeof(double) * c->nfft) != cudaSuccess ||
-        cudaMalloc((void **)&c->adj_flag, sizeof(int)) != cudaSuccess) {
-        cudaGetLastError();
-        return VP_ERR_OOM;
+        if (cudaMalloc(&c->adj_f, cs * 3 * c->np) != cudaSuccess ||   // K1 table of the replay
+            cudaMalloc((void **)&c->adj_g, sizeof(double) * 3 * c->np) != cudaSuccess ||
+            cudaMalloc((void **)&c->adj_lg, sizeof(double) * 3 * c->np) != cudaSuccess ||
+            cudaMalloc((void **)&c->adj_tmp, sizeof(double) * c->nfft) != cudaSuccess) {
+            cudaGetLastError();
+            return VP_ERR_OOM;
+        }
     }
-    return VP_OK;
+    if (c->adj_mode != 1 && alloc_adjoint_states(c, 9)) return VP_OK;
+    if (c->adj_mode == 2) return VP_ERR_OOM;
+    return alloc_adjoint_states(c, 2) ? VP_OK : VP_ERR_OOM;
 }
 
 // scalar on the device used as the replay's tau
@@ -760,6 +784,87 @@ int vp_functional(vp_ctx *c, int kind, const double *target, void *lambda_f, dou
     return VP_OK;
 }
 
+int vp_set_adjoint_states(vp_ctx *c, int mode)
+{
+    if (!c || mode < 0 || mode > 2) return VP_ERR_ARG;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return VP_ERR_CUDA;
+    }
+    free_adjoint_states(c);
+    c->adj_mode = mode;
+    return VP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// sweeps 0..2 (K1) of the replay from S0 into dst, in one launch sequence
+int replay_k1(vp_ctx *c, const void *S0, void *dst, const void *k1)
+{
+    void *src = const_cast<void *>(S0);
+    if (vp_kick_fast_ok(c)) {
+        VP_CUDA_TRY(launch_kick_fast(c, src, k1, nullptr, 3, 0, dst));
+    } else if (vp_kick_big_ok(c)) {
+        VP_CUDA_TRY(launch_kick_big(c, src, k1, nullptr, 3, 0, dst));
+    } else {
+        VP_CUDA_TRY(cudaMemcpyAsync(dst, S0, (size_t)c->ncells * c->esize, cudaMemcpyDeviceToDevice,
+                                    c->stream));
+        VP_CUDA_TRY(launch_kick(c, dst, k1, nullptr, 3, 0));
+    }
+    return VP_OK;
+}
+
+// The adjoint step with two scratch states X, Y: the sweep inputs S1..S8
+// are recomputed from S0 = f_start in four partial replays, each leaving two
+// consecutive inputs in X and Y: (S7, S8) [and g^{n+1} on the way], (S5,
+// S6), (S3, S4), (S1, S2).  The adjoint sweeps run in reverse order between
+// the replays.
+int adjoint_step_two_states(vp_ctx *c, const void *S0, void *lambda_f, double *lambda_g,
+                            const void *k1, const double *tau_ptr, double dt, double amax)
+{
+    void *X = c->adj_states[0], *Y = c->adj_states[1];
+    const double tau = 0.5 * dt;
+    // replay to (S7, S8); the density of S6 gives g^{n+1}
+    TRY(replay_k1(c, S0, X, k1));                                                 // X = S3
+    VP_CUDA_TRY(launch_sweep_into(c, X, Y, 2, c->coef_drift, amax));              // Y = S4
+    VP_CUDA_TRY(launch_sweep_into(c, Y, X, 1, c->coef_drift, amax));              // X = S5
+    VP_CUDA_TRY(launch_sweep_into(c, X, Y, 0, c->coef_drift, amax));              // Y = S6
+    VP_CUDA_TRY(launch_density(c, Y, c->rho2));
+    VP_CUDA_TRY(launch_field_solve(c, c->rho2, c->adj_g));
+    VP_CUDA_TRY(launch_coef_kick(c, c->adj_g, tau_ptr, 0.5, c->coef_kick2));
+    VP_CUDA_TRY(launch_sweep_into(c, Y, X, 3, c->coef_kick2, amax));              // X = S7
+    VP_CUDA_TRY(launch_sweep_into(c, X, Y, 4, c->coef_kick2, amax));              // Y = S8
+    VP_CUDA_TRY(launch_kick_adjoint(c, Y, lambda_f, 2, c->coef_kick2, tau, lambda_g));
+    VP_CUDA_TRY(launch_kick_adjoint(c, X, lambda_f, 1, c->coef_kick2, tau, lambda_g));
+    // replay to (S5, S6)
+    TRY(replay_k1(c, S0, X, k1));
+    VP_CUDA_TRY(launch_sweep_into(c, X, Y, 2, c->coef_drift, amax));
+    VP_CUDA_TRY(launch_sweep_into(c, Y, X, 1, c->coef_drift, amax));              // X = S5
+    VP_CUDA_TRY(launch_sweep_into(c, X, Y, 0, c->coef_drift, amax));              // Y = S6
+    VP_CUDA_TRY(launch_kick_adjoint(c, Y, lambda_f, 0, c->coef_kick2, tau, lambda_g));
+    VP_CUDA_TRY(launch_field_adjoint(c, lambda_g, lambda_f, true));
+    VP_CUDA_TRY(launch_drift_adjoint(c, X, lambda_f, 0, c->coef_drift, c->rho2));
+    // replay to (S3, S4)
+    TRY(replay_k1(c, S0, X, k1));                                                 // X = S3
+    VP_CUDA_TRY(launch_sweep_into(c, X, Y, 2, c->coef_drift, amax));              // Y = S4
+    VP_CUDA_TRY(launch_drift_adjoint(c, Y, lambda_f, 1, c->coef_drift, nullptr));
+    VP_CUDA_TRY(launch_drift_adjoint(c, X, lambda_f, 2, c->coef_drift, nullptr));
+    // replay to (S1, S2)
+    VP_CUDA_TRY(cudaMemsetAsync(lambda_g, 0, sizeof(double) * 3 * c->np, c->stream));
+    VP_CUDA_TRY(launch_sweep_into(c, S0, X, 3, k1, amax));                        // X = S1
+    VP_CUDA_TRY(launch_sweep_into(c, X, Y, 4, k1, amax));                         // Y = S2
+    VP_CUDA_TRY(launch_kick_adjoint(c, Y, lambda_f, 2, k1, tau, lambda_g));
+    VP_CUDA_TRY(launch_kick_adjoint(c, X, lambda_f, 1, k1, tau, lambda_g));
+    VP_CUDA_TRY(launch_kick_adjoint(c, S0, lambda_f, 0, k1, tau, lambda_g));
+    return VP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int vp_adjoint_step(vp_ctx *c, const void *f_start, const double *g_start, void *lambda_f,
                     double *lambda_g)
 {
@@ -780,6 +885,12 @@ int vp_adjoint_step(vp_ctx *c, const void *f_start, const double *g_start, void 
     VP_CUDA_TRY(launch_coef_drift(c, tau_ptr, 1.0, c->coef_drift));
     const double amax = vp_drift_alpha_bound(c, dt);
     const void *S0 = f_start;     // S[k]: input of sweep k of the step (S[0] = f^n)
+    if (c->adj_nstates == 2) {
+        const int r = adjoint_step_two_states(c, S0, lambda_f, lambda_g, k1, tau_ptr, dt, amax);
+        VP_CUDA_TRY(cudaMemcpyAsync(&c->sc->lost, &c->sc->pad[1], sizeof(double),
+                                    cudaMemcpyDeviceToDevice, c->stream));
+        return r;
+    }
     const bool reg = vp_kick_adjoint3_ok(c);
     // --- forward replay
     if (reg) {

@@ -94,8 +94,9 @@ struct vp_ctx {
     double *adj_lg;             // 3 np
     double *adj_tmp;            // nfft
     int *adj_flag;              // set when the register adjoint skipped a line
-    void **adj_states;          // nine sweep inputs (f's dtype)
+    void **adj_states;          // sweep inputs (f's dtype): nine, or two to recompute into
     int adj_nstates;
+    int adj_mode;               // 0 automatic, 1 two states, 2 nine states
 };
 
 // ---------------------------------------------------------------------------
@@ -135,7 +136,7 @@ int vp_rho_parts(vp_ctx *c);
 // consecutive vy / vz sweeps, lines in registers
 int vp_kick_big_ok(const vp_ctx *c);
 cudaError_t launch_kick_big(vp_ctx *c, void *f, const void *ca, const void *cb, int nsweeps,
-                            int first_axis);
+                            int first_axis, void *fo = nullptr);
 // fused z then y drift of the whole grid (in place when fo == f); fz, if not
 // null, also receives the z sweep's output (fz != f)
 int vp_drift_yz_ok(const vp_ctx *c);

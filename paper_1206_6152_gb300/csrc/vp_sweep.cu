@@ -654,6 +654,8 @@ cudaError_t launch_sweep_into(vp_ctx *c, const void *src, void *dst, int axis, c
 {
     if (axis >= 3 && vp_kick_fast_ok(c))
         return launch_kick_fast(c, const_cast<void *>(src), coef, nullptr, 1, axis - 3, dst);
+    if (axis >= 3 && vp_kick_big_ok(c))
+        return launch_kick_big(c, const_cast<void *>(src), coef, nullptr, 1, axis - 3, dst);
     if (axis < 3 && vp_drift_fast_ok(c, axis) && drift_alpha_bound < 1.0)
         return launch_drift_fast(c, const_cast<void *>(src), axis, coef, nullptr, dst);
     cudaError_t e = cudaMemcpyAsync(dst, src, (size_t)c->ncells * c->esize,

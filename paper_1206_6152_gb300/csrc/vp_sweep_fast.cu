@@ -429,9 +429,10 @@ __global__ void __launch_bounds__(KickCube<N>::NT) k_kick6(float *__restrict__ f
 // A line with a whole-cell shift takes the generic in-place routine.
 // ---------------------------------------------------------------------------
 template <int N>
-__global__ void __launch_bounds__(128) k_kick_vx_big(float *__restrict__ f,
+__global__ void __launch_bounds__(128) k_kick_vx_big(const float *__restrict__ f,
                                                     const LineCoef<float> *__restrict__ coef,
-                                                    long long np, double *lost_out)
+                                                    long long np, double *lost_out,
+                                                    float *__restrict__ fo)
 {
     __shared__ Acc<double> red[32];
     constexpr int H = N / 2;
@@ -441,17 +442,21 @@ __global__ void __launch_bounds__(128) k_kick_vx_big(float *__restrict__ f,
     float lost = 0.f;
     if (u < N * H) {
         const LineCoef<float> cf = coef[cell * 3];
-        float *g = f + cell * (long long)N * N * N + (u / H) * N + 2 * (u % H);
-        if ((cf.code >> 1) == 0) {
-            float2 x[N];
+        const long long off = cell * (long long)N * N * N + (u / H) * N + 2 * (u % H);
+        const float *g = f + off;
+        float *go = fo + off;
+        float2 x[N];
 #pragma unroll
-            for (int i = 0; i < N; ++i) x[i] = *reinterpret_cast<const float2 *>(g + i * N * N);
+        for (int i = 0; i < N; ++i) x[i] = *reinterpret_cast<const float2 *>(g + i * N * N);
+        if ((cf.code >> 1) == 0) {
             lost += sweep_pairs<N>(x, cf);
 #pragma unroll
-            for (int i = 0; i < N; ++i) *reinterpret_cast<float2 *>(g + i * N * N) = x[i];
+            for (int i = 0; i < N; ++i) *reinterpret_cast<float2 *>(go + i * N * N) = x[i];
         } else {
-            lost += kick_line_shifted(g, N * N, N, cf);
-            lost += kick_line_shifted(g + 1, N * N, N, cf);
+#pragma unroll
+            for (int i = 0; i < N; ++i) *reinterpret_cast<float2 *>(go + i * N * N) = x[i];
+            lost += kick_line_shifted(go, N * N, N, cf);
+            lost += kick_line_shifted(go + 1, N * N, N, cf);
         }
     }
     Acc<double> a;
@@ -468,8 +473,9 @@ struct PlaneBig {
 
 template <int N>
 __global__ void __launch_bounds__(PlaneBig<N>::NT, 3) k_kick_plane_big(
-    float *__restrict__ f, const LineCoef<float> *__restrict__ c0, int a0,
-    const LineCoef<float> *__restrict__ c1, int a1, int nsw, double *lost_out)
+    const float *__restrict__ f, const LineCoef<float> *__restrict__ c0, int a0,
+    const LineCoef<float> *__restrict__ c1, int a1, int nsw, double *lost_out,
+    float *__restrict__ fo)
 {
     constexpr int P = PlaneBig<N>::P, PPC = PlaneBig<N>::PPC, NT = PlaneBig<N>::NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -478,7 +484,8 @@ __global__ void __launch_bounds__(PlaneBig<N>::NT, 3) k_kick_plane_big(
     const int t = threadIdx.x, pl = t / N, m = t % N;
     const long long cell = blockIdx.x;
     const int i0 = blockIdx.y * PPC;                      // first plane of the CTA
-    float *g = f + (cell * N + i0) * (long long)N * N;   // PPC contiguous planes
+    const float *g = f + (cell * N + i0) * (long long)N * N;   // PPC contiguous planes
+    float *go = fo + (cell * N + i0) * (long long)N * N;
     // thread t moves column t % N of rows t / N, t / N + NT / N, ... (the
     // PPC planes are PPC * N contiguous rows)
     constexpr int RS = NT / N, NR = PPC * N / RS;         // rows per step, rows per thread
@@ -517,7 +524,7 @@ __global__ void __launch_bounds__(PlaneBig<N>::NT, 3) k_kick_plane_big(
         const float *tp = tile + (t / N) * P + m;
 #pragma unroll
         for (int i = 0; i < NR; ++i) v[i] = tp[i * RS * P];
-        float *gp = g + (t / N) * N + m;
+        float *gp = go + (t / N) * N + m;
 #pragma unroll
         for (int i = 0; i < NR; ++i) gp[i * RS * N] = v[i];
     }
@@ -966,10 +973,11 @@ int vp_kick_big_ok(const vp_ctx *c)
 }
 
 cudaError_t launch_kick_big(vp_ctx *c, void *f_, const void *ca_, const void *cb_, int nsweeps,
-                            int first_axis)
+                            int first_axis, void *fo_)
 {
     constexpr int N = 48;
     float *f = (float *)f_;
+    float *fo = fo_ ? (float *)fo_ : f;   // the first pass reads f, every pass writes fo
     const LineCoef<float> *ca = (const LineCoef<float> *)ca_, *cb = (const LineCoef<float> *)cb_;
     cudaError_t e;
     for (int sw = 0; sw < nsweeps;) {
@@ -977,7 +985,7 @@ cudaError_t launch_kick_big(vp_ctx *c, void *f_, const void *ca_, const void *cb
         const LineCoef<float> *cf = sw < 3 ? ca : cb;
         if (va == 0) {
             const dim3 grid((unsigned)c->np, (unsigned)((N * N / 2 + 127) / 128));
-            k_kick_vx_big<N><<<grid, 128, 0, c->stream>>>(f, cf, c->np, &c->sc->lost);
+            k_kick_vx_big<N><<<grid, 128, 0, c->stream>>>(sw ? fo : f, cf, c->np, &c->sc->lost, fo);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             ++sw;
             continue;
@@ -990,8 +998,9 @@ cudaError_t launch_kick_big(vp_ctx *c, void *f_, const void *ca_, const void *cb
                                       (int)PB::SMEM)) != cudaSuccess)
             return e;
         const dim3 grid((unsigned)c->np, (unsigned)(N / PB::PPC));
-        k_kick_plane_big<N><<<grid, PB::NT, PB::SMEM, c->stream>>>(f, cf, va, sw + 1 < 3 ? ca : cb, vb,
-                                                                   nsw, &c->sc->lost);
+        k_kick_plane_big<N><<<grid, PB::NT, PB::SMEM, c->stream>>>(sw ? fo : f, cf, va,
+                                                                   sw + 1 < 3 ? ca : cb, vb, nsw,
+                                                                   &c->sc->lost, fo);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         sw += nsw;
     }

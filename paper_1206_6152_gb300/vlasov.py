@@ -160,6 +160,11 @@ class VlasovPoisson:
         check(self.lib.vp_adjoint_step(self._ctx, _ptr(f_start), _ptr(g_start), _ptr(lam_f),
                                        _ptr(lam_g)), "vp_adjoint_step")
 
+    def set_adjoint_states(self, mode: int) -> None:
+        """Scratch policy of adjoint_step: 0 automatic, 1 two states
+        (recompute), 2 nine states."""
+        check(self.lib.vp_set_adjoint_states(self._ctx, int(mode)), "vp_set_adjoint_states")
+
     def sweep_adjoint(self, axis: int, tau: float, f_in: torch.Tensor, lam: torch.Tensor,
                       lam_g: Optional[torch.Tensor] = None) -> None:
         check(self.lib.vp_sweep_adjoint(self._ctx, int(axis), float(tau), _ptr(f_in), _ptr(lam),

@@ -107,8 +107,9 @@ def test_register_adjoint_sweeps_match_oracle(dtype, shape, space_bc):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("states", [0, 1])
 @pytest.mark.parametrize("bc", ["periodic", "isolated"])
-def test_adjoint_step_matches_oracle(bc):
+def test_adjoint_step_matches_oracle(bc, states):
     w = I.small_maxwell(n=(6, 5, 4), nv=(8, 7, 6), dtype="f64", amp=0.2, G=20.0)
     w = w.replace(dt_fixed=0.01)
     if bc == "isolated":
@@ -118,6 +119,7 @@ def test_adjoint_step_matches_oracle(bc):
     rng = np.random.default_rng(3)
     f0 = I.initial_condition(w) * (1 + 0.2 * rng.random(w.shape))
     sim, f = gpu_sim(w, f0)
+    sim.set_adjoint_states(states)           # 1: inputs recomputed with two states
     g0 = sim.field()[2]
     lam_f = torch.from_numpy(rng.normal(size=w.shape)).to(DEV)
     lam_g = torch.from_numpy(rng.normal(size=(3,) + w.n)).to(DEV)
@@ -133,8 +135,10 @@ def test_adjoint_step_matches_oracle(bc):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("G,n", [(20.0, (16, 2, 2)), (200.0, (16, 2, 2)), (20.0, (2, 16, 16))])
-def test_adjoint_step_fp32_register_kernels_match_oracle(G, n):
+@pytest.mark.parametrize("G,n,states", [(20.0, (16, 2, 2), 0), (200.0, (16, 2, 2), 0),
+                                        (20.0, (2, 16, 16), 0), (20.0, (16, 2, 2), 1),
+                                        (2000.0, (2, 16, 16), 1)])
+def test_adjoint_step_fp32_register_kernels_match_oracle(G, n, states):
     """FP32 adjoint step on grids served by the packed kernels against the
     FP64 oracle's adjoint step: x lines of 16 with the density broadcast
     added on load, 16^3 velocity cubes (vz input recomputed); y and z lines
@@ -149,6 +153,7 @@ def test_adjoint_step_fp32_register_kernels_match_oracle(G, n):
     rng = np.random.default_rng(4)
     f0 = (I.initial_condition(w, np.float64) * (1 + 0.2 * rng.random(w.shape))).astype(np.float32)
     sim, f = gpu_sim(w, f0)
+    sim.set_adjoint_states(states)
     g0 = sim.field()[2]
     lam_f = torch.from_numpy(rng.normal(size=w.shape).astype(np.float32)).to(DEV)
     lam_g = torch.from_numpy(rng.normal(size=(3,) + w.n)).to(DEV)
@@ -162,6 +167,33 @@ def test_adjoint_step_fp32_register_kernels_match_oracle(G, n):
     got_f, got_g = lam_f.cpu().numpy().astype(np.float64), lam_g.cpu().numpy()
     if G > 100:
         assert np.abs(osim.g).max() * 0.5 * w.dt_fixed / grid.dv[0] > 1.5   # whole-cell kicks
+    assert np.abs(got_f - rf).sum() / np.abs(rf).sum() <= 2e-5
+    assert np.abs(got_g - rg).sum() / np.abs(rg).sum() <= 2e-5
+    sim.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("states", [0, 1])
+def test_adjoint_step_48_cubes_match_oracle(states):
+    """FP32 adjoint step with 48^3 velocity cubes (out-of-place replay kicks,
+    per-axis register adjoints over any number of cubes) against the FP64
+    oracle, with nine kept states and with two."""
+    w = I.large_c5().replace(n=(2, 2, 2), box_lo=(-0.5,) * 3, box_hi=(0.5,) * 3, G=40.0,
+                             dt_fixed=0.01)
+    grid = O.Grid.of(w)
+    rng = np.random.default_rng(8)
+    f0 = (I.initial_condition(w, np.float64) * (1 + 0.2 * rng.random(w.shape))).astype(np.float32)
+    sim, f = gpu_sim(w, f0)
+    sim.set_adjoint_states(states)
+    g0 = sim.field()[2]
+    lam_f = torch.from_numpy(rng.normal(size=w.shape).astype(np.float32)).to(DEV)
+    lam_g = torch.from_numpy(rng.normal(size=(3,) + w.n)).to(DEV)
+    lf0, lg0 = lam_f.cpu().numpy().astype(np.float64), lam_g.cpu().numpy()
+    sim.adjoint_step(torch.from_numpy(f0).to(DEV), g0, lam_f, lam_g)
+    f64 = f0.astype(np.float64)
+    osim = O.Simulation(f64, grid, O.Params.of(w))
+    rf, rg = O.adjoint_step(osim, f64, osim.g, lf0, lg0)
+    got_f, got_g = lam_f.cpu().numpy().astype(np.float64), lam_g.cpu().numpy()
     assert np.abs(got_f - rf).sum() / np.abs(rf).sum() <= 2e-5
     assert np.abs(got_g - rg).sum() / np.abs(rg).sum() <= 2e-5
     sim.close()
