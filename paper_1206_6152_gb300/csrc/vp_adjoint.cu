@@ -301,22 +301,26 @@ cudaError_t launch_broadcast(vp_ctx *c, const double *bc, T *lam)
 // lam_f = scale * w[cell] broadcast over velocity, w = phi (kind 0) or
 // rho - target (kind 1)
 template <typename T>
-__global__ void k_functional_grad(T *__restrict__ lam_f, const double *__restrict__ phi,
-                                  const double *__restrict__ rho, const double *__restrict__ target,
-                                  int kind, long long nvc, int n1, int n2, int f1, int f2,
-                                  double scale, long long ncells)
+__global__ void __launch_bounds__(256) k_functional_grad(T *__restrict__ lam_f,
+                                                        const double *__restrict__ phi,
+                                                        const double *__restrict__ rho,
+                                                        const double *__restrict__ target, int kind,
+                                                        long long nvc, int n1, int n2, int f1,
+                                                        int f2, double scale, long long np)
 {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ncells) return;
-    const long long cell = t / nvc;
-    double w;
-    if (kind == 0) {
-        const int k = (int)(cell % n2), j = (int)((cell / n2) % n1), i = (int)(cell / ((long long)n1 * n2));
-        w = phi[((long long)i * f1 + j) * f2 + k];
-    } else {
-        w = rho[cell] - target[cell];
+    for (long long cell = blockIdx.x; cell < np; cell += gridDim.x) {
+        double w;
+        if (kind == 0) {
+            const int k = (int)(cell % n2), j = (int)((cell / n2) % n1);
+            const int i = (int)(cell / ((long long)n1 * n2));
+            w = phi[((long long)i * f1 + j) * f2 + k];
+        } else {
+            w = rho[cell] - target[cell];
+        }
+        const T v = (T)(w * scale);
+        T *q = lam_f + cell * nvc;
+        for (long long e = threadIdx.x; e < nvc; e += blockDim.x) q[e] = v;
     }
-    lam_f[t] = (T)(w * scale);
 }
 
 // sum (rho - target)^2 (compensated), one CTA
@@ -768,14 +772,16 @@ int vp_functional(vp_ctx *c, int kind, const double *target, void *lambda_f, dou
         VP_CUDA_TRY(cudaGetLastError());
     }
     const double scale = c->dvol_v * c->dvol_x;
+    long long grid = 8LL * vp_sm_count();
+    if (grid > c->np) grid = c->np;
     if (c->isdouble)
-        k_functional_grad<double><<<nblk(c->ncells, T), T, 0, c->stream>>>(
+        k_functional_grad<double><<<(unsigned)grid, T, 0, c->stream>>>(
             (double *)lambda_f, c->phi, c->rho2, target, kind, c->nvc, c->n[1], c->n[2], c->fn[1],
-            c->fn[2], scale, c->ncells);
+            c->fn[2], scale, c->np);
     else
-        k_functional_grad<float><<<nblk(c->ncells, T), T, 0, c->stream>>>(
+        k_functional_grad<float><<<(unsigned)grid, T, 0, c->stream>>>(
             (float *)lambda_f, c->phi, c->rho2, target, kind, c->nvc, c->n[1], c->n[2], c->fn[1],
-            c->fn[2], scale, c->ncells);
+            c->fn[2], scale, c->np);
     VP_CUDA_TRY(cudaGetLastError());
     double h;
     VP_CUDA_TRY(cudaMemcpyAsync(&h, sums, sizeof(double), cudaMemcpyDeviceToHost, c->stream));

@@ -217,8 +217,8 @@ def _J_of(sim, f0, nsteps, kind, target):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("kind", [0, 1])
-def test_trajectory_gradient_fp64_matches_fd(kind):
+@pytest.mark.parametrize("kind,keep", [(0, None), (1, None), (0, False)])
+def test_trajectory_gradient_fp64_matches_fd(kind, keep):
     from paper_1206_6152_gb300.adjoint import trajectory_functional
     w = I.small_maxwell(n=(8, 6, 5), nv=(10, 8, 9), dtype="f64", amp=0.1, G=25.0)
     w = w.replace(dt_fixed=0.008)
@@ -230,7 +230,7 @@ def test_trajectory_gradient_fp64_matches_fd(kind):
     nsteps = 6
     amps = amps0.clone().requires_grad_(True)
     J = trajectory_functional(_mode_f0(w, amps, torch.float64), sim, nsteps, every=4, kind=kind,
-                              target=target)
+                              target=target, keep_states=keep)
     J.backward()
     grad = amps.grad.cpu().numpy()
     for m in range(len(w.modes)):
