@@ -46,10 +46,13 @@ int vp_sm_count();
 
 namespace {
 
+// per-line weights of the adjoint: K0 = c0 + 2 (c1 - c2); with c' = dc/dbeta
+// the beta derivative of phi_j is f_j + c1' E+ + c2' E-
+//   = kf f_j + Fd1 s1 + Fd2 s2,  kf = 1 + 2 (c1' - c2'), Fd1 = -F c1', Fd2 = F c2'
 template <typename V>
 struct AdjW {
-    V K0, c1, c2, dc1, dc2;    // K0 = c0 + 2 (c1 - c2); dc = dc/dbeta
-    V F, ninvF, r3;
+    V K0, c1, c2, kf, Fd1, Fd2;
+    V ninvF, r3;
 };
 
 __device__ __forceinline__ float sel1(bool p) { return p ? 1.f : 0.f; }
@@ -83,25 +86,28 @@ struct AOps<float> {
 };
 
 __device__ __forceinline__ void adj_weights1(const LineCoef<float> &cf, float finf, float &K0,
-                                             float &c1, float &c2, float &dc1, float &dc2,
-                                             float &F, float &ninvF)
+                                             float &c1, float &c2, float &kf, float &Fd1,
+                                             float &Fd2, float &ninvF)
 {
     float A1, A2;
     weights1<float>(cf.c0, cf.c1, cf.c2, cf.code & 1, finf, K0, A1, A2, ninvF);
     const float beta = cf.c0;
     c1 = cf.c1;
     c2 = cf.c2;
-    dc1 = (2.f - 6.f * beta + 3.f * beta * beta) * (1.f / 6.f);
-    dc2 = (1.f - 3.f * beta * beta) * (1.f / 6.f);
-    F = finf + finf;
+    const float dc1 = (2.f - 6.f * beta + 3.f * beta * beta) * (1.f / 6.f);
+    const float dc2 = (1.f - 3.f * beta * beta) * (1.f / 6.f);
+    const float F = finf + finf;
+    kf = 1.f + 2.f * (dc1 - dc2);
+    Fd1 = -F * dc1;
+    Fd2 = F * dc2;
 }
 
 __device__ __forceinline__ AdjW<float2> adj_weights(const LineCoef<float> &ca,
                                                     const LineCoef<float> &cb, float2 finf)
 {
     AdjW<float2> w;
-    adj_weights1(ca, finf.x, w.K0.x, w.c1.x, w.c2.x, w.dc1.x, w.dc2.x, w.F.x, w.ninvF.x);
-    adj_weights1(cb, finf.y, w.K0.y, w.c1.y, w.c2.y, w.dc1.y, w.dc2.y, w.F.y, w.ninvF.y);
+    adj_weights1(ca, finf.x, w.K0.x, w.c1.x, w.c2.x, w.kf.x, w.Fd1.x, w.Fd2.x, w.ninvF.x);
+    adj_weights1(cb, finf.y, w.K0.y, w.c1.y, w.c2.y, w.kf.y, w.Fd1.y, w.Fd2.y, w.ninvF.y);
     w.r3 = __fmul2_rn(w.ninvF, make_float2(-3.f, -3.f));
     return w;
 }
@@ -109,7 +115,7 @@ __device__ __forceinline__ AdjW<float2> adj_weights(const LineCoef<float> &ca,
 __device__ __forceinline__ AdjW<float> adj_weights(const LineCoef<float> &cf, float finf)
 {
     AdjW<float> w;
-    adj_weights1(cf, finf, w.K0, w.c1, w.c2, w.dc1, w.dc2, w.F, w.ninvF);
+    adj_weights1(cf, finf, w.K0, w.c1, w.c2, w.kf, w.Fd1, w.Fd2, w.ninvF);
     w.r3 = w.ninvF * -3.f;
     return w;
 }
@@ -157,11 +163,7 @@ __device__ __forceinline__ void adjoint_line(const V (&f)[N], V (&l)[N], const A
         lF = O::fma(a, O::fma(u1, i1, O::mul(s1, mone)), lF);      // a (u1 I1 - s1)
         lF = O::fma(b, O::fma(O::mul(u2, mone), i2, s2), lF);      // b (s2 - u2 I2)
         if (DB) {
-            const V two_f = O::add(f0, f0);
-            const V ep = O::fma(O::mul(w.F, mone), s1, two_f);      // 2 f - F s1
-            const V em = O::fma(w.F, s2, O::mul(two_f, mone));      // F s2 - 2 f
-            V e = O::fma(w.dc1, ep, f0);
-            e = O::fma(w.dc2, em, e);
+            const V e = O::fma(w.Fd2, s2, O::fma(w.Fd1, s1, O::mul(w.kf, f0)));
             db = O::fma(mu, e, db);
         }
         hprev = hcur;
@@ -213,11 +215,7 @@ __device__ __forceinline__ void adjoint_line_mem(const V (&f)[N], const V *lsrc,
         lF = O::fma(a, O::fma(u1, i1, O::mul(s1, mone)), lF);
         lF = O::fma(b, O::fma(O::mul(u2, mone), i2, s2), lF);
         if (DB) {
-            const V two_f = O::add(f0, f0);
-            const V ep = O::fma(O::mul(w.F, mone), s1, two_f);
-            const V em = O::fma(w.F, s2, O::mul(two_f, mone));
-            V e = O::fma(w.dc1, ep, f0);
-            e = O::fma(w.dc2, em, e);
+            const V e = O::fma(w.Fd2, s2, O::fma(w.Fd1, s1, O::mul(w.kf, f0)));
             db = O::fma(mu, e, db);
         }
         hprev = hcur;
@@ -310,6 +308,7 @@ struct PairGeom {
     long long m1, m2;
     int va_stride, va_n;       // velocity index along the axis: (v / va_stride) % va_n
     int zremap, nvz;           // z drift: pairs per half vz row of the warp-uniform map (0: off)
+    int mixed;                 // z drift: some pair (v, v + 1) has v_z of both signs
     long long units;           // line pairs per outer index (drift) or per cube (kick)
     long long per_part;        // units per CTA (drift)
     // kick axes: pair p -> voff = (p / pd) pm_hi + 2 (p % pd), element stride vstride
@@ -610,7 +609,7 @@ cudaError_t pairs_n(vp_ctx *c, const float *fin, float *lam, const LineCoef<floa
     else if (bc)
         k_adjoint_pairs<N, PERIODIC, false, true, false><<<grid, 128, 0, c->stream>>>(
             fin, lam, coef, g, bc, lam_g, scale, sk);
-    else if (g.axis == 2)
+    else if (g.axis == 2 && g.mixed)
         k_adjoint_pairs<N, PERIODIC, false, false, true><<<grid, 128, 0, c->stream>>>(
             fin, lam, coef, g, bc, lam_g, scale, sk);
     else
@@ -706,6 +705,14 @@ cudaError_t launch_adjoint_pairs(vp_ctx *c, const void *fin_, void *lam_, int ax
         g.va_n = c->nv[axis];
         g.units = c->nvc / 2;
         g.nvz = c->nv[2];
+        if (axis == 2) {
+            // the directions of the two lines of a pair (2m, 2m + 1) differ only
+            // where the cell centres straddle v_z = 0 (tau has one sign)
+            const double vl = c->cfg.vlo[2], dvz = c->dv[2];
+            auto sgn = [](double v) { return v < 0.0 ? -1 : (v > 0.0 ? 1 : 0); };
+            for (int k = 0; k + 1 < c->nv[2]; k += 2)
+                if (sgn(vl + (k + 0.5) * dvz) != sgn(vl + (k + 1.5) * dvz)) g.mixed = 1;
+        }
         if (axis == 2 && c->nv[2] % 4 == 0) {
             const int H = c->nv[2] / 4;
             if (32 % H == 0 && ((long long)c->nv[0] * c->nv[1]) % (2 * (32 / H)) == 0) g.zremap = H;
