@@ -939,9 +939,13 @@ int vp_adjoint_step(vp_ctx *c, const void *f_start, const double *g_start, void 
     // adjoint as it loads lambda_f
     VP_CUDA_TRY(launch_field_adjoint(c, lambda_g, lambda_f, true));
     // drift x, y, z reversed
-    for (int k = 5; k >= 3; --k)
-        VP_CUDA_TRY(launch_drift_adjoint(c, S[k], lambda_f, 5 - k, c->coef_drift,
-                                         k == 5 ? c->rho2 : nullptr));
+    VP_CUDA_TRY(launch_drift_adjoint(c, S[5], lambda_f, 0, c->coef_drift, c->rho2));
+    if (amax < 1.0 && vp_drift_adjoint_yz_ok(c)) {
+        VP_CUDA_TRY(launch_drift_adjoint_yz(c, S[4], S[3], lambda_f, c->coef_drift));
+    } else {
+        VP_CUDA_TRY(launch_drift_adjoint(c, S[4], lambda_f, 1, c->coef_drift, nullptr));
+        VP_CUDA_TRY(launch_drift_adjoint(c, S[3], lambda_f, 2, c->coef_drift, nullptr));
+    }
     // K1 reversed; its g-cotangent is that of g^n
     VP_CUDA_TRY(cudaMemsetAsync(lambda_g, 0, sizeof(double) * 3 * c->np, c->stream));
     TRY(kick_adjoint3(c, S0, S[1], reg ? nullptr : S[2], S[2], lambda_f, k1, 0.5 * dt, lambda_g));

@@ -597,6 +597,101 @@ __global__ void __launch_bounds__(128) k_kick_adjoint_zy(const float *__restrict
     }
 }
 
+// The y and then the z drift adjoint in one pass (FP32, N_y = N_z = N, 16
+// (N = 32) or 32 (N = 16) velocity cells per CTA, zero-shift drifts), the
+// transpose of k_drift_yz: the y adjoint reads its lines (pairs of adjacent
+// velocity cells) of the cotangent and of the y input straight from global
+// memory and writes the result to a shared tile [y][z][VC]; the z adjoint
+// reads its cotangent lines from the tile and the z input from global memory
+// and writes the result back.  The cotangent crosses HBM once for the two
+// sweeps.  Pairs of z lines with directions of both signs go through the
+// scalar path.
+template <int N>
+struct AdjYZ {
+    static constexpr int VC = 512 / N, NT = N * VC / 2;
+    static constexpr int YP = N * VC + (VC == 16 ? 16 : 0);
+    static constexpr size_t SMEM = (size_t)N * YP * sizeof(float);
+};
+
+template <int N, bool PERIODIC>
+__global__ void __launch_bounds__(AdjYZ<N>::NT, 1) k_drift_adjoint_yz(
+    const float *__restrict__ s4, const float *__restrict__ s3, float *__restrict__ lam,
+    const LineCoef<float> *__restrict__ cz, const LineCoef<float> *__restrict__ cy, long long nvc,
+    int nvy, int nvz)
+{
+    constexpr int VC = AdjYZ<N>::VC, YP = AdjYZ<N>::YP, H = VC / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *tile = reinterpret_cast<float *>(smem_raw);
+    const int t = threadIdx.x, vp = t % H, r = t / H;    // r: z in the y adjoint, y in the z adjoint
+    const long long v0 = (long long)blockIdx.x * VC;
+    const long long x0 = (long long)blockIdx.y * N * N;
+    const long long v = v0 + 2 * vp;
+    {
+        // y adjoint: line (z = r, v pair), cells y = 0..N-1
+        const long long off = (x0 + r) * nvc + v;
+        float2 f[N], l[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            f[j] = *reinterpret_cast<const float2 *>(s4 + off + (long long)j * N * nvc);
+            l[j] = *reinterpret_cast<const float2 *>(lam + off + (long long)j * N * nvc);
+        }
+        const LineCoef<float> c = cy[(int)((v0 / nvz) % nvy)];
+        const float2 finf = line_max(f);
+        const AdjW<float2> w = adj_weights(c, c, finf);
+        float2 lF, db;
+        const bool neg = c.code & 1;
+        if (neg) adjoint_line<float2, N, PERIODIC, true, false>(f, l, w, lF, db);
+        else adjoint_line<float2, N, PERIODIC, false, false>(f, l, w, lF, db);
+        const int2 am = first_max2<N>(f, finf, neg);
+        float *q = tile + r * VC + 2 * vp;              // tile [y][z][vc]
+#pragma unroll
+        for (int j = 0; j < N; ++j) *reinterpret_cast<float2 *>(q + j * YP) = l[j];
+        q[am.x * YP] += 2.f * lF.x;
+        q[am.y * YP + 1] += 2.f * lF.y;
+    }
+    __syncthreads();
+    {
+        // z adjoint: line (y = r, v pair), cells z = 0..N-1
+        const long long off = (x0 + (long long)r * N) * nvc + v;
+        float2 f[N], l[N];
+        const float *q = tile + r * YP + 2 * vp;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            f[j] = *reinterpret_cast<const float2 *>(s3 + off + (long long)j * nvc);
+            l[j] = *reinterpret_cast<const float2 *>(q + j * VC);
+        }
+        const LineCoef<float> ca = cz[(int)(v % nvz)], cb = cz[(int)((v + 1) % nvz)];
+        int ax, ay;
+        float lfx, lfy;
+        if ((ca.code & 1) == (cb.code & 1)) {
+            const float2 finf = line_max(f);
+            const AdjW<float2> w = adj_weights(ca, cb, finf);
+            float2 lF, db;
+            const bool neg = ca.code & 1;
+            if (neg) adjoint_line<float2, N, PERIODIC, true, false>(f, l, w, lF, db);
+            else adjoint_line<float2, N, PERIODIC, false, false>(f, l, w, lF, db);
+            const int2 am = first_max2<N>(f, finf, neg);
+            ax = am.x; ay = am.y;
+            lfx = 2.f * lF.x; lfy = 2.f * lF.y;
+        } else {
+            float2 fm[N], lm[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) { fm[j] = f[j]; lm[j] = l[j]; }
+            int am[2];
+            float lfm[2];
+            adjoint_pair_mixed<N, PERIODIC, false>(fm, lm, ca, cb, am, lfm);
+            ax = am[0]; ay = am[1];
+            lfx = lfm[0]; lfy = lfm[1];
+#pragma unroll
+            for (int j = 0; j < N; ++j) l[j] = lm[j];
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) *reinterpret_cast<float2 *>(lam + off + (long long)j * nvc) = l[j];
+        lam[off + (long long)ax * nvc] += lfx;
+        lam[off + (long long)ay * nvc + 1] += lfy;
+    }
+}
+
 template <int N, bool PERIODIC>
 cudaError_t pairs_n(vp_ctx *c, const float *fin, float *lam, const LineCoef<float> *coef,
                     const PairGeom &g, dim3 grid, const double *bc, double *lam_g, double scale)
@@ -668,6 +763,44 @@ cudaError_t launch_kick_adjoint3(vp_ctx *c, const void *sa, const void *sb, void
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return launch_adjoint_pairs(c, sa, lam, 3, coef, lam_g, tau / c->dv[0], nullptr, 1);
+}
+
+// the y then z drift adjoints in one pass (zero-shift drifts: the caller
+// checks the shift bound); s4, s3 the inputs of the y and z drifts
+int vp_drift_adjoint_yz_ok(const vp_ctx *c)
+{
+    if (c->isdouble || c->n[1] != c->n[2]) return 0;
+    const int n = c->n[1];
+    if (n != 16 && n != 32) return 0;
+    return c->nv[2] % (512 / n) == 0 && c->n[0] <= 65535;
+}
+
+cudaError_t launch_drift_adjoint_yz(vp_ctx *c, const void *s4, const void *s3, void *lam,
+                                    const void *coef)
+{
+    const LineCoef<float> *cf = (const LineCoef<float> *)coef;
+    const LineCoef<float> *cz = cf + (size_t)2 * c->maxnv, *cy = cf + (size_t)c->maxnv;
+    const float *a = (const float *)s4, *b = (const float *)s3;
+    float *l = (float *)lam;
+    cudaError_t e;
+    if (c->n[1] == 32) {
+        typedef AdjYZ<32> K;
+        const dim3 grid((unsigned)(c->nvc / K::VC), (unsigned)c->n[0]);
+        auto k = c->periodic_space ? k_drift_adjoint_yz<32, true> : k_drift_adjoint_yz<32, false>;
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM)) !=
+            cudaSuccess)
+            return e;
+        k<<<grid, K::NT, K::SMEM, c->stream>>>(a, b, l, cz, cy, c->nvc, c->nv[1], c->nv[2]);
+    } else {
+        typedef AdjYZ<16> K;
+        const dim3 grid((unsigned)(c->nvc / K::VC), (unsigned)c->n[0]);
+        auto k = c->periodic_space ? k_drift_adjoint_yz<16, true> : k_drift_adjoint_yz<16, false>;
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM)) !=
+            cudaSuccess)
+            return e;
+        k<<<grid, K::NT, K::SMEM, c->stream>>>(a, b, l, cz, cy, c->nvc, c->nv[1], c->nv[2]);
+    }
+    return cudaGetLastError();
 }
 
 int vp_adjoint_pairs_ok(const vp_ctx *c, int axis)
