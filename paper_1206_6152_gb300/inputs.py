@@ -215,8 +215,16 @@ def jeans48_slab() -> Workload:
     return large_c5().replace(name="jeans48_slab_f32", n=(8, 8, 8))
 
 
+def adjoint_profile() -> Workload:
+    """The fixed-dt 3-mode Jeans set-up on 16^3 positions (537 MB of FP32 f):
+    the adjoint kernels of the 32^3 x 32^3 adjoint workload at line and cube
+    length 32 (x lines 16), for hardware-counter captures."""
+    return adjoint_c4().replace(name="jeans16x32_modes3", n=(16, 16, 16))
+
+
 WORKLOADS = {
     "jeans16x32_f32": jeans_profile,
+    "jeans16x32_modes3": adjoint_profile,
     "jeans48_slab_f32": jeans48_slab,
     "jeans_slab_yz_f32": jeans_slab_yz,
     "jeans_slab_x_f32": jeans_slab_x,
