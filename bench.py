@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--adjoint-steps", type=int, default=3)
     p.add_argument("--adjoint-workload", default="jeans32_modes3")
+    p.add_argument("--fp64-steps", type=int, default=20)
     p.add_argument("--cpu-sample", type=float, default=1.0 / 64)
     return p.parse_args()
 
@@ -334,6 +335,11 @@ def run_ours(args, ranks: Ranks):
         "kernel_ms": {k: round(v, 4) for k, v in avg.items()},
         "step_bytes_algorithmic": len(fams) * bytes_rw,
         "step_hbm_frac": round(len(fams) * bytes_rw / (avg["step"] / 1e3) / 1e9 / peak, 4),
+        # the step against the bandwidth bound of the three-pass plan (24 B
+        # per cell for FP32) and of the method's floor (f read and written
+        # once per step, 8 B per cell)
+        "step_frac_of_3pass_bound": round(3 * bytes_rw / (avg["step"] / 1e3) / 1e9 / peak, 4),
+        "step_frac_of_1pass_floor": round(bytes_rw / (avg["step"] / 1e3) / 1e9 / peak, 4),
     }
 
     # end to end through the host-buffer entry point: every step copies its
@@ -358,6 +364,11 @@ def run_ours(args, ranks: Ranks):
 
     # adjoint / forward time per step on the fixed-dt workload of the same
     # grid (the adjoint step replays its forward step, then reverses it)
+    # the FP64-storage workload (16^3 x 16^3 Landau box), same timing rules
+    fp64 = None
+    if args.fp64_steps > 0 and w.dtype == "f32":
+        fp64 = time_fp64(args, dev, stream, ranks)
+
     adjoint = None
     if args.adjoint_steps > 0:
         adjoint = time_adjoint(args, dev, stream)
@@ -378,9 +389,32 @@ def run_ours(args, ranks: Ranks):
                    "l2": "inputs larger than L2 (f is %.1f GB)" % (w.cells * esize / 1e9),
                    "parallelism": "replicas" if ranks.world > 1 else "single GPU"},
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
-        "adjoint": adjoint, "cpu_baseline": cpu,
+        "adjoint": adjoint, "fp64": fp64, "cpu_baseline": cpu,
     }
     return out
+
+
+def time_fp64(args, dev, stream, ranks):
+    """Cell-updates/s of the FP64-storage Landau workload (16^3 x 16^3), timed
+    like the main line (graph replay, CUDA events, warm-up excluded)."""
+    import torch
+    from paper_1206_6152_gb300 import inputs as I
+    from paper_1206_6152_gb300.vlasov import VlasovPoisson, config_of
+    w = I.landau_c1()
+    f = torch.from_numpy(I.initial_condition(w)).to(dev)
+    sim = VlasovPoisson(config_of(w), f, stream)
+    sim.step(3)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.fp64_steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ranks.max(e0.elapsed_time(e1)) / args.fp64_steps
+    sim.close()
+    return {"workload": w.name, "dtype": "f64", "ms_per_step": round(ms, 4),
+            "value": ranks.world * w.cells / (ms / 1e3), "unit": UNIT,
+            "note": "f is 134 MB (near L2 size); FP64 register kernels for lines of 16"}
 
 
 def time_adjoint(args, dev, stream):

@@ -1,0 +1,145 @@
+"""The one-dimensional tests of Sec. 3.1-3.3 (Tests 1-3) run through the 6D
+GPU library on degenerate grids (one cell along y, z, vy, vz), FP64 storage:
+
+* Test 1: periodic free streaming of a top hat (G = 0), against the oracle
+  step by step, with mass, positivity and the maximum principle;
+* Test 2: the linear Jeans growth rate (k/k_J = 0.5) and the gravitational
+  Landau damping rate (k/k_J = 1.5) against the roots of the Maxwellian
+  dispersion relation, and the density-mode amplitude against the oracle;
+* Test 3: the same growth with the Maxwellian moving at v_t = sigma and
+  2 sigma (Galilean invariance: the rate does not change).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytestmark = pytest.mark.skip(reason="needs a CUDA GPU")
+
+from oracle import vp_oracle as O  # noqa: E402
+from paper_1206_6152_gb300 import inputs as I  # noqa: E402
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1206_6152_gb300 import build as B
+    B.build()
+
+
+def sim_1d(f2, L, V, G, courant=0.5, dt_fixed=0.0):
+    from paper_1206_6152_gb300.vlasov import VlasovPoisson, make_config
+    nx, nv = f2.shape
+    cfg = make_config((nx, 1, 1), (nv, 1, 1), (-L / 2, -0.5, -0.5), (L / 2, 0.5, 0.5),
+                      (-V, -0.5, -0.5), (V, 0.5, 0.5), G=G, courant=courant, dt_fixed=dt_fixed,
+                      dtype=torch.float64)
+    f = torch.from_numpy(np.ascontiguousarray(f2.reshape(nx, 1, 1, nv, 1, 1))).to(DEV)
+    return VlasovPoisson(cfg, f), f
+
+
+def grid_1d(nx, nv, L, V):
+    return O.Grid((nx, 1, 1), (nv, 1, 1), (-L / 2, -0.5, -0.5), (L / 2, 0.5, 0.5),
+                  (-V, -0.5, -0.5), (V, 0.5, 0.5))
+
+
+@pytest.mark.gpu
+def test_top_hat_free_streaming_matches_oracle():
+    nx, nv = 128, 128
+    f0, x, v = I.top_hat_1d(nx, nv)
+    dt = 0.37 * (1.0 / nx) / 1.0                    # non-integer Courant numbers
+    sim, f = sim_1d(f0, 1.0, 1.0, G=0.0, dt_fixed=dt)
+    ref = O.Simulation(f0.reshape(nx, 1, 1, nv, 1, 1).copy(), grid_1d(nx, nv, 1.0, 1.0),
+                       O.Params(G=0.0, courant=0.5, dt_fixed=dt))
+    M0 = f0.sum()
+    for _ in range(5):
+        sim.step(8)
+        ref.step(8)
+        got = f.cpu().numpy().reshape(nx, nv)
+        assert np.abs(got - ref.f.reshape(nx, nv)).max() <= 1e-12
+    assert abs(got.sum() - M0) <= 1e-12 * M0
+    assert got.min() >= 0.0 and got.max() <= 1.0 + 1e-13
+    sim.close()
+
+
+def maxwell_1d(nx, nv, k_over_kj, amp, vt=0.0, n_mode=2):
+    """Test 2 set-up: L = 1, G = 1, rho_bar = 1, v in [-1, 1]; sigma from k_J."""
+    L, G, rho_bar, V = 1.0, 1.0, 1.0, 1.0
+    k = 2 * math.pi * n_mode / L
+    kj = k / k_over_kj
+    sigma = math.sqrt(4 * math.pi * G * rho_bar) / kj
+    x = -L / 2 + (np.arange(nx) + 0.5) * (L / nx)
+    v = -V + (np.arange(nv) + 0.5) * (2 * V / nv)
+    f = rho_bar * (1 + amp * np.cos(k * x))[:, None] \
+        * np.exp(-(v - vt) ** 2 / (2 * sigma ** 2))[None, :] / math.sqrt(2 * math.pi * sigma ** 2)
+    return f, sigma, k
+
+
+def mode_amplitude(rho, n_mode=2):
+    rho = np.asarray(rho).reshape(-1)
+    return abs(np.fft.fft(rho / rho.mean() - 1)[n_mode]) * 2 / rho.size
+
+
+def run_gpu(f0, t_end):
+    sim, f = sim_1d(f0, 1.0, 1.0, G=1.0)
+    ts, amps = [], []
+    t = 0.0
+    while t < t_end:
+        ts.append(t)
+        amps.append(mode_amplitude(sim.density().cpu().numpy()))
+        t = sim.step(1, sync=True)
+    sim.close()
+    return np.array(ts), np.array(amps)
+
+
+def growth_root(kk):
+    from scipy.optimize import brentq
+    from scipy.special import erfcx
+    return brentq(lambda y: 1 - math.sqrt(math.pi) * y * erfcx(y) - kk ** 2, 1e-9, 50)
+
+
+def damping_root(kk):
+    from scipy.optimize import brentq
+    return brentq(lambda y: 1 + math.sqrt(math.pi) * y * math.exp(y * y) * (1 + math.erf(y))
+                  - kk ** 2, 1e-12, 5)
+
+
+@pytest.mark.gpu
+def test_jeans_growth_matches_theory_and_oracle():
+    f0, sigma, k = maxwell_1d(64, 128, 0.5, 0.01)
+    ts, amps = run_gpu(f0, 0.9)
+    gamma = growth_root(0.5) * math.sqrt(2) * k * sigma
+    sel = (ts > 0.3) & (ts < 0.9)
+    assert np.polyfit(ts[sel], np.log(amps[sel]), 1)[0] == pytest.approx(gamma, rel=0.05)
+    # the oracle's trajectory, first 40 steps
+    ref = O.Simulation(f0.reshape(64, 1, 1, 128, 1, 1).copy(), grid_1d(64, 128, 1.0, 1.0),
+                       O.Params(G=1.0, courant=0.5))
+    for n in range(40):
+        assert abs(ref.t - ts[n]) <= 1e-12 * max(ts[n], 1.0)
+        assert mode_amplitude(O.density(ref.f, ref.grid)) == pytest.approx(amps[n], rel=1e-9)
+        ref.step()
+
+
+@pytest.mark.gpu
+def test_landau_damping_matches_theory():
+    f0, sigma, k = maxwell_1d(64, 128, 1.5, 0.01)
+    ts, amps = run_gpu(f0, 0.85)
+    gamma = damping_root(1.5) * math.sqrt(2) * k * sigma
+    sel = (ts > 0.25) & (ts < 0.8)
+    assert -np.polyfit(ts[sel], np.log(amps[sel]), 1)[0] == pytest.approx(gamma, rel=0.07)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("vt_over_sigma", [1.0, 2.0])
+def test_galilean_shift_keeps_the_growth_rate(vt_over_sigma):
+    f0, sigma, k = maxwell_1d(64, 128, 0.5, 0.01)
+    f1, _s, _k = maxwell_1d(64, 128, 0.5, 0.01, vt=vt_over_sigma * sigma)
+    t0, a0 = run_gpu(f0, 0.9)
+    t1, a1 = run_gpu(f1, 0.9)
+    s0 = (t0 > 0.3) & (t0 < 0.9)
+    s1 = (t1 > 0.3) & (t1 < 0.9)
+    g0 = np.polyfit(t0[s0], np.log(a0[s0]), 1)[0]
+    g1 = np.polyfit(t1[s1], np.log(a1[s1]), 1)[0]
+    assert g1 == pytest.approx(g0, rel=0.05)
