@@ -50,11 +50,12 @@ class Workload:
     steps: int = 1
     seed: int = 0
     # initial condition
-    ic: str = "maxwell"                # "maxwell" | "king"
+    ic: str = "maxwell"                # "maxwell" | "king" | "noise"
     rho_bar: float = 1.0
     sigma: float = 1.0
     modes: Tuple[Tuple[Tuple[int, int, int], float, float], ...] = ()
     king_w0: float = 6.0
+    noise_amp: float = 0.0             # ic "noise": rms of the white-noise density contrast
 
     # -- geometry (problem definition, Sec. 2) --------------------------
     @property
@@ -196,6 +197,20 @@ def jeans_profile() -> Workload:
     return jeans_c2().replace(name="jeans16x32_f32", n=(16, 16, 16))
 
 
+def white_noise32(kj_over_k1: float = 4.0) -> Workload:
+    """Test 4 (Sec. 3.4): 32^3 x 32^3 FP32 periodic box (L = 1, G = 1,
+    sigma = 1, v in [-5, 5]^3) with a white-noise density contrast of rms
+    1e-4 (seed 4); rho_bar sets the Jeans wavenumber k_J = kj_over_k1 * 2 pi / L
+    (4: k_J = 8 pi / L, 8: 16 pi / L)."""
+    L, sigma = 1.0, 1.0
+    kj = kj_over_k1 * 2 * math.pi / L
+    return Workload(
+        name="white_noise32_kj%d" % int(kj_over_k1), n=(32, 32, 32), nv=(32, 32, 32),
+        box_lo=(-L / 2,) * 3, box_hi=(L / 2,) * 3, vlo=(-5.0,) * 3, vhi=(5.0,) * 3,
+        G=1.0, courant=0.5, dtype="f32", steps=200, seed=4, ic="noise",
+        rho_bar=kj * kj * sigma * sigma / (4 * math.pi), sigma=sigma, noise_amp=1e-4)
+
+
 def jeans_slab_yz() -> Workload:
     """A 4-plane slab (4 x 32 x 32 spatial cells) of the 32^3 x 32^3 Jeans
     box: the fused z + y drift at its full-size line length 32, with 537 MB
@@ -233,6 +248,7 @@ WORKLOADS = {
     "king64x32_w6": king_c3,
     "jeans32_modes3": adjoint_c4,
     "jeans48_modes8": large_c5,
+    "white_noise32_kj4": white_noise32,
 }
 
 
@@ -255,7 +271,12 @@ def mode_fields(w: Workload) -> np.ndarray:
 
 
 def density_contrast(w: Workload, amplitudes: Optional[Sequence[float]] = None) -> np.ndarray:
-    """delta(x) = sum_m A_m cos(k_m . x + theta_m) on the spatial centres."""
+    """delta(x) = sum_m A_m cos(k_m . x + theta_m) on the spatial centres, or
+    for ic "noise" white noise: independent Gaussian cell values of rms
+    noise_amp (seeded PCG64), with their mean removed."""
+    if w.ic == "noise":
+        d = np.random.default_rng(w.seed).normal(0.0, w.noise_amp, size=w.n)
+        return d - d.mean()
     if not w.modes:
         return np.zeros(w.n)
     amps = [m[1] for m in w.modes] if amplitudes is None else list(amplitudes)

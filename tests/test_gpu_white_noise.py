@@ -1,0 +1,78 @@
+"""Test 4 (Sec. 3.4): a white-noise density field on the 32^3 x 32^3 FP32 box
+with k_J = 8 pi / L.  In the linear regime every Fourier mode of the
+density contrast evolves with the root of the Maxwellian dispersion relation
+for its |k|: modes with k < k_J grow, modes with k > k_J are Landau-damped.
+The power P(k, t) of each exact |n|^2 class (one |k| per class) is followed
+step by step and its logarithmic slope compared with 2 gamma(k)."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytestmark = pytest.mark.skip(reason="needs a CUDA GPU")
+
+from paper_1206_6152_gb300 import inputs as I  # noqa: E402
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1206_6152_gb300 import build as B
+    B.build()
+
+
+def growth_root(kk):
+    from scipy.optimize import brentq
+    from scipy.special import erfcx
+    return brentq(lambda y: 1 - math.sqrt(math.pi) * y * erfcx(y) - kk ** 2, 1e-9, 50)
+
+
+def damping_root(kk):
+    from scipy.optimize import brentq
+    return brentq(lambda y: 1 + math.sqrt(math.pi) * y * math.exp(y * y) * (1 + math.erf(y))
+                  - kk ** 2, 1e-12, 5)
+
+
+@pytest.mark.gpu
+@pytest.mark.slow
+def test_white_noise_power_grows_and_damps_at_linear_rates():
+    from paper_1206_6152_gb300.vlasov import VlasovPoisson, config_of
+    w = I.white_noise32()                       # k_J = 8 pi / L
+    L = w.box_hi[0] - w.box_lo[0]
+    kj = math.sqrt(4 * math.pi * w.G * w.rho_bar) / w.sigma
+    f = torch.from_numpy(I.initial_condition(w)).to(DEV)
+    sim = VlasovPoisson(config_of(w), f)
+    n = torch.fft.fftfreq(32, d=1.0 / 32, device=DEV).round()
+    n2 = (n[:, None, None] ** 2 + n[None, :, None] ** 2 + n[None, None, :] ** 2)
+    classes = {1: None, 4: None, 36: None}      # k/k_J = 0.25, 0.5, 1.5
+    masks = {c: (n2 == c) for c in classes}
+
+    def power():
+        rho = sim.density()
+        d = rho / rho.mean() - 1.0
+        p = torch.fft.fftn(d).abs() ** 2
+        return {c: float(p[m].mean()) for c, m in masks.items()}
+
+    ts, ps = [], []
+    t = 0.0
+    while t < 0.3:
+        ts.append(t)
+        ps.append(power())
+        t = sim.step(1, sync=True)
+    sim.close()
+    ts = np.array(ts)
+    for c in classes:
+        k = 2 * math.pi / L * math.sqrt(c)
+        kk = k / kj
+        logp = np.log(np.array([p[c] for p in ps]) / ps[0][c])
+        if kk < 1:
+            gamma = growth_root(kk) * math.sqrt(2) * k * w.sigma
+            sel = (ts > 0.12) & (ts < 0.3)
+            assert np.polyfit(ts[sel], logp[sel], 1)[0] == pytest.approx(2 * gamma, rel=0.1), c
+        else:
+            gamma = damping_root(kk) * math.sqrt(2) * k * w.sigma
+            sel = (ts > 0.03) & (ts < 0.12)
+            assert -np.polyfit(ts[sel], logp[sel], 1)[0] == pytest.approx(2 * gamma, rel=0.2), c
