@@ -50,12 +50,14 @@ class Workload:
     steps: int = 1
     seed: int = 0
     # initial condition
-    ic: str = "maxwell"                # "maxwell" | "king" | "noise"
+    ic: str = "maxwell"                # "maxwell" | "king" | "king2" | "noise"
     rho_bar: float = 1.0
     sigma: float = 1.0
     modes: Tuple[Tuple[Tuple[int, int, int], float, float], ...] = ()
     king_w0: float = 6.0
     noise_amp: float = 0.0             # ic "noise": rms of the white-noise density contrast
+    king_sep: float = 0.0              # ic "king2": centre separation along x (r0 units)
+    king_u: float = 0.0                # ic "king2": each sphere's speed towards the other
 
     # -- geometry (problem definition, Sec. 2) --------------------------
     @property
@@ -154,6 +156,25 @@ def king_c3(w0: float = 6.0, n: int = 64, nv: int = 32) -> Workload:
         dtype="f32", steps=300, seed=0, ic="king", sigma=1.0, king_w0=w0)
 
 
+def king_merger(w0: float = 3.0, nv: int = 32) -> Workload:
+    """Two King spheres (W0 = 3) on the x axis, centres 2.2 r_t apart,
+    approaching each other at 0.5 sigma_c each (the Vlasov side of the merger
+    runs of Sec. 3.6).  64 x 32 x 32 cubic cells over a box of half-widths
+    (2.15 r_t, 1.075 r_t, 1.075 r_t), velocities within 3 sigma_c + u,
+    isolated Poisson, outflow boundaries, FP32."""
+    prof = king_profile(w0)
+    sep = 2.2 * prof.r_t
+    u = 0.5 * prof.sigma_c
+    hx, hy = 2.15 * prof.r_t, 1.075 * prof.r_t
+    vb = 3.0 * prof.sigma_c + u
+    return Workload(
+        name=f"king_merger_w{w0:g}", n=(64, 32, 32), nv=(nv,) * 3,
+        box_lo=(-hx, -hy, -hy), box_hi=(hx, hy, hy), vlo=(-vb,) * 3, vhi=(vb,) * 3,
+        G=1.0, courant=0.5, space_bc="outflow", poisson_bc="isolated",
+        dtype="f32", steps=200, seed=0, ic="king2", sigma=1.0, king_w0=w0,
+        king_sep=sep, king_u=u)
+
+
 def adjoint_c4() -> Workload:
     """Jeans setup with 3 random modes (seed 1), 100 steps, fixed dt."""
     L = 1.0
@@ -249,6 +270,7 @@ WORKLOADS = {
     "jeans32_modes3": adjoint_c4,
     "jeans48_modes8": large_c5,
     "white_noise32_kj4": white_noise32,
+    "king_merger_w3": king_merger,
 }
 
 
@@ -307,7 +329,7 @@ def initial_condition(w: Workload, dtype=None, amplitudes=None) -> np.ndarray:
     """f(x, v, t=0) on the cell centres, C order [x][y][z][vx][vy][vz].
     Computed in FP64 and rounded once to the storage type."""
     dt = np.dtype(dtype or ("float32" if w.dtype == "f32" else "float64"))
-    if w.ic == "king":
+    if w.ic in ("king", "king2"):
         return king_initial_condition(w, dt)
     rho_x, mv = factors(w, amplitudes)
     out = np.empty((int(np.prod(w.n)), mv.size), dtype=dt)
@@ -397,19 +419,32 @@ def king_profile(w0: float = 6.0) -> KingProfile:
 
 
 def king_initial_condition(w: Workload, dtype) -> np.ndarray:
-    """King DF at the cell centres, before the virial renormalisation."""
+    """King DF at the cell centres, before the virial renormalisation; for
+    ic "king2" the sum of two King spheres centred at x = -+ king_sep / 2 and
+    moving at v_x = +- king_u (towards each other)."""
     prof = king_profile(w.king_w0)
     xs = [w.centres_x(a) for a in range(3)]
-    r = np.sqrt(xs[0][:, None, None] ** 2 + xs[1][None, :, None] ** 2
-                + xs[2][None, None, :] ** 2)
-    psi = prof.psi(r).reshape(-1)                      # sigma = 1
     vx, vy, vz = (w.centres_v(a) for a in range(3))
-    v2 = (vx[:, None, None] ** 2 + vy[None, :, None] ** 2 + vz[None, None, :] ** 2).reshape(-1)
     norm = prof.rho1 * (2 * math.pi) ** -1.5
-    out = np.empty((psi.size, v2.size), dtype=dtype)
-    step = max(1, (1 << 24) // v2.size)
-    for s in range(0, psi.size, step):
-        e = min(psi.size, s + step)
-        E = psi[s:e, None] - 0.5 * v2[None, :]
-        out[s:e] = (norm * np.where(E > 0, np.expm1(np.maximum(E, 0.0)), 0.0)).astype(dtype)
+    if w.ic == "king2":
+        spheres = ((-0.5 * w.king_sep, w.king_u), (0.5 * w.king_sep, -w.king_u))
+    else:
+        spheres = ((0.0, 0.0),)
+    psis, v2s = [], []
+    for cx, ux in spheres:
+        r = np.sqrt((xs[0][:, None, None] - cx) ** 2 + xs[1][None, :, None] ** 2
+                    + xs[2][None, None, :] ** 2)
+        psis.append(prof.psi(r).reshape(-1))             # sigma = 1
+        v2s.append(((vx - ux)[:, None, None] ** 2 + vy[None, :, None] ** 2
+                    + vz[None, None, :] ** 2).reshape(-1))
+    npos, nvel = psis[0].size, v2s[0].size
+    out = np.empty((npos, nvel), dtype=dtype)
+    step = max(1, (1 << 24) // nvel)
+    for s in range(0, npos, step):
+        e = min(npos, s + step)
+        acc = np.zeros((e - s, nvel))
+        for psi, v2 in zip(psis, v2s):
+            E = psi[s:e, None] - 0.5 * v2[None, :]
+            acc += np.where(E > 0, np.expm1(np.maximum(E, 0.0)), 0.0)
+        out[s:e] = (norm * acc).astype(dtype)
     return out.reshape(w.shape)

@@ -96,3 +96,35 @@ def test_king64x32_one_dynamical_time():
     assert e1["M_out"] <= 2.5e-4 * M0
     assert np.abs(enclosed_mass() - m0).max() <= 1e-2 * M0
     sim.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.slow
+def test_king_merger_accounting_and_approach():
+    """Two W0 = 3 King spheres approaching each other (the Vlasov side of the
+    merger of Sec. 3.6) on 64 x 32 x 32 x 32^3 cells (2.1e9, FP32): mass
+    accounting through the velocity and position bounds to 1e-8, f >= 0,
+    the mirror symmetry x -> -x (centre of mass at 0), and the two density
+    peaks moving towards each other."""
+    w = I.king_merger()
+    f0 = I.initial_condition(w)
+    sim, f = gpu_sim(w, f0, torch.float32)
+    del f0
+    x = w.centres_x(0)
+
+    def peaks():
+        p = sim.density().sum(dim=(1, 2)).cpu().numpy()
+        left, right = np.argmax(np.where(x < 0, p, -1)), np.argmax(np.where(x > 0, p, -1))
+        return x[right] - x[left], float((x * p).sum() / p.sum())
+
+    M0 = sim.energy()["M"]
+    sep0, cm0 = peaks()
+    for _ in range(5):
+        sim.step(20)
+        e = sim.energy()
+        assert abs(e["M"] + e["M_out"] - M0) <= 1e-8 * M0
+    sep, cm = peaks()
+    assert float(f.min()) >= 0.0
+    assert abs(cm0) <= 1e-6 * w.dx[0] and abs(cm) <= 1e-3 * w.dx[0]
+    assert sep <= sep0 - 4 * w.dx[0]
+    sim.close()
