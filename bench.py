@@ -244,7 +244,7 @@ def load_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("vp_sweep.cu", "vp_sweep_fast.cu", "vp_line.cuh", "vp_device.cuh"):
+    for name in ("vp_sweep.cu", "vp_sweep_fast.cu", "vp_fast_line.cuh", "vp_line.cuh", "vp_device.cuh"):
         with open(os.path.join(ROOT, "paper_1206_6152_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -852,11 +852,15 @@ int adjoint_step_two_states(vp_ctx *c, const void *S0, void *lambda_f, double *l
     VP_CUDA_TRY(launch_kick_adjoint(c, Y, lambda_f, 0, c->coef_kick2, tau, lambda_g));
     VP_CUDA_TRY(launch_field_adjoint(c, lambda_g, lambda_f, true));
     VP_CUDA_TRY(launch_drift_adjoint(c, X, lambda_f, 0, c->coef_drift, c->rho2));
-    // replay to (S3, S4)
+    // replay to S3 (and S4, unless the fused y+z adjoint recomputes it)
     TRY(replay_k1(c, S0, X, k1));                                                 // X = S3
-    VP_CUDA_TRY(launch_sweep_into(c, X, Y, 2, c->coef_drift, amax));              // Y = S4
-    VP_CUDA_TRY(launch_drift_adjoint(c, Y, lambda_f, 1, c->coef_drift, nullptr));
-    VP_CUDA_TRY(launch_drift_adjoint(c, X, lambda_f, 2, c->coef_drift, nullptr));
+    if (amax < 1.0 && vp_drift_yz_ok(c)) {
+        VP_CUDA_TRY(launch_drift_adjoint_yz(c, X, lambda_f, c->coef_drift));
+    } else {
+        VP_CUDA_TRY(launch_sweep_into(c, X, Y, 2, c->coef_drift, amax));          // Y = S4
+        VP_CUDA_TRY(launch_drift_adjoint(c, Y, lambda_f, 1, c->coef_drift, nullptr));
+        VP_CUDA_TRY(launch_drift_adjoint(c, X, lambda_f, 2, c->coef_drift, nullptr));
+    }
     // replay to (S1, S2)
     VP_CUDA_TRY(cudaMemsetAsync(lambda_g, 0, sizeof(double) * 3 * c->np, c->stream));
     VP_CUDA_TRY(launch_sweep_into(c, S0, X, 3, k1, amax));                        // X = S1
@@ -908,8 +912,11 @@ int vp_adjoint_step(vp_ctx *c, const void *f_start, const double *g_start, void 
         for (int k = 0; k < 3; ++k)
             VP_CUDA_TRY(launch_sweep_into(c, k ? S[k] : S0, S[k + 1], 3 + k, k1, amax));
     }
-    if (amax < 1.0 && vp_drift_yz_ok(c)) {
-        VP_CUDA_TRY(launch_drift_yz(c, S[3], c->coef_drift, S[5], S[4]));
+    // the fused y+z drift adjoint recomputes the y input S4 from S3: the
+    // replay then keeps S5 only
+    const bool yz = amax < 1.0 && vp_drift_yz_ok(c);
+    if (yz) {
+        VP_CUDA_TRY(launch_drift_yz(c, S[3], c->coef_drift, S[5], nullptr));
     } else {
         VP_CUDA_TRY(launch_sweep_into(c, S[3], S[4], 2, c->coef_drift, amax));
         VP_CUDA_TRY(launch_sweep_into(c, S[4], S[5], 1, c->coef_drift, amax));
@@ -940,8 +947,8 @@ int vp_adjoint_step(vp_ctx *c, const void *f_start, const double *g_start, void 
     VP_CUDA_TRY(launch_field_adjoint(c, lambda_g, lambda_f, true));
     // drift x, y, z reversed
     VP_CUDA_TRY(launch_drift_adjoint(c, S[5], lambda_f, 0, c->coef_drift, c->rho2));
-    if (amax < 1.0 && vp_drift_adjoint_yz_ok(c)) {
-        VP_CUDA_TRY(launch_drift_adjoint_yz(c, S[4], S[3], lambda_f, c->coef_drift));
+    if (yz) {
+        VP_CUDA_TRY(launch_drift_adjoint_yz(c, S[3], lambda_f, c->coef_drift));
     } else {
         VP_CUDA_TRY(launch_drift_adjoint(c, S[4], lambda_f, 1, c->coef_drift, nullptr));
         VP_CUDA_TRY(launch_drift_adjoint(c, S[3], lambda_f, 2, c->coef_drift, nullptr));

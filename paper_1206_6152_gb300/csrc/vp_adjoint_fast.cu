@@ -38,6 +38,7 @@
 
 #include "vp_device.cuh"
 #include "vp_internal.cuh"
+#include "vp_fast_line.cuh"
 #include "vp_line.cuh"
 
 using namespace vpline;
@@ -46,33 +47,26 @@ int vp_sm_count();
 
 namespace {
 
-// per-line weights of the adjoint: K0 = c0 + 2 (c1 - c2); with c' = dc/dbeta
-// the beta derivative of phi_j is f_j + c1' E+ + c2' E-
+// per-line weights of the adjoint: K0 = c0 + 2 (c1 - c2), the cotangent
+// weights 3 c1, -3 c2, -c1, c2 of the frozen-arm terms, and with c' = dc/dbeta
+// the beta derivative of phi_j, f_j + c1' E+ + c2' E-
 //   = kf f_j + Fd1 s1 + Fd2 s2,  kf = 1 + 2 (c1' - c2'), Fd1 = -F c1', Fd2 = F c2'
 template <typename V>
 struct AdjW {
-    V K0, c1, c2, kf, Fd1, Fd2;
+    V K0, c3a, c3b, nc1, c2, kf, Fd1, Fd2;
     V ninvF, r3;
 };
 
-__device__ __forceinline__ float sel1(bool p) { return p ? 1.f : 0.f; }
-
-// forward weights of one line (as the forward kernels)
-template <typename S>
-__device__ __forceinline__ LineW<S> weights_one(const LineCoef<S> &cf, S finf)
-{
-    LineW<S> w;
-    weights1<S>(cf.c0, cf.c1, cf.c2, cf.code & 1, finf, w.K0, w.A1, w.A2, w.ninvF);
-    return w;
-}
+__device__ __forceinline__ float nsel1(bool p) { return p ? -1.f : 0.f; }
 
 template <typename V>
 struct AOps;
 template <>
 struct AOps<float2> {
-    __device__ __forceinline__ static float2 eq(float2 a, float2 b)
+    // -[a == b]
+    __device__ __forceinline__ static float2 neq(float2 a, float2 b)
     {
-        return make_float2(sel1(a.x == b.x), sel1(a.y == b.y));
+        return make_float2(nsel1(a.x == b.x), nsel1(a.y == b.y));
     }
     __device__ __forceinline__ static float2 fsat(float2 a, float2 b, float2 c)
     {
@@ -81,18 +75,20 @@ struct AOps<float2> {
 };
 template <>
 struct AOps<float> {
-    __device__ __forceinline__ static float eq(float a, float b) { return sel1(a == b); }
+    __device__ __forceinline__ static float neq(float a, float b) { return nsel1(a == b); }
     __device__ __forceinline__ static float fsat(float a, float b, float c) { return fmasat(a, b, c); }
 };
 
 __device__ __forceinline__ void adj_weights1(const LineCoef<float> &cf, float finf, float &K0,
-                                             float &c1, float &c2, float &kf, float &Fd1,
-                                             float &Fd2, float &ninvF)
+                                             float &c3a, float &c3b, float &nc1, float &c2,
+                                             float &kf, float &Fd1, float &Fd2, float &ninvF)
 {
     float A1, A2;
     weights1<float>(cf.c0, cf.c1, cf.c2, cf.code & 1, finf, K0, A1, A2, ninvF);
     const float beta = cf.c0;
-    c1 = cf.c1;
+    c3a = 3.f * cf.c1;
+    c3b = -3.f * cf.c2;
+    nc1 = -cf.c1;
     c2 = cf.c2;
     const float dc1 = (2.f - 6.f * beta + 3.f * beta * beta) * (1.f / 6.f);
     const float dc2 = (1.f - 3.f * beta * beta) * (1.f / 6.f);
@@ -106,8 +102,10 @@ __device__ __forceinline__ AdjW<float2> adj_weights(const LineCoef<float> &ca,
                                                     const LineCoef<float> &cb, float2 finf)
 {
     AdjW<float2> w;
-    adj_weights1(ca, finf.x, w.K0.x, w.c1.x, w.c2.x, w.kf.x, w.Fd1.x, w.Fd2.x, w.ninvF.x);
-    adj_weights1(cb, finf.y, w.K0.y, w.c1.y, w.c2.y, w.kf.y, w.Fd1.y, w.Fd2.y, w.ninvF.y);
+    adj_weights1(ca, finf.x, w.K0.x, w.c3a.x, w.c3b.x, w.nc1.x, w.c2.x, w.kf.x, w.Fd1.x, w.Fd2.x,
+                 w.ninvF.x);
+    adj_weights1(cb, finf.y, w.K0.y, w.c3a.y, w.c3b.y, w.nc1.y, w.c2.y, w.kf.y, w.Fd1.y, w.Fd2.y,
+                 w.ninvF.y);
     w.r3 = __fmul2_rn(w.ninvF, make_float2(-3.f, -3.f));
     return w;
 }
@@ -115,187 +113,198 @@ __device__ __forceinline__ AdjW<float2> adj_weights(const LineCoef<float> &ca,
 __device__ __forceinline__ AdjW<float> adj_weights(const LineCoef<float> &cf, float finf)
 {
     AdjW<float> w;
-    adj_weights1(cf, finf, w.K0, w.c1, w.c2, w.kf, w.Fd1, w.Fd2, w.ninvF);
+    adj_weights1(cf, finf, w.K0, w.c3a, w.c3b, w.nc1, w.c2, w.kf, w.Fd1, w.Fd2, w.ninvF);
     w.r3 = w.ninvF * -3.f;
     return w;
 }
 
-// Cotangent of the zero-shift update of the line f (read-only) given the
-// output cotangent l, which is overwritten with the input cotangent (without
-// the f_inf term: l_F is returned for the caller to place).  Array index of
-// upwind position j: j (u > 0) or N - 1 - j (u < 0).
-template <typename V, int N, bool PERIODIC, bool NEG, bool DB>
-__device__ __forceinline__ void adjoint_line(const V (&f)[N], V (&l)[N], const AdjW<V> &w, V &lF,
-                                             V &db)
-{
-    typedef VOps<V> O;
-    typedef AOps<V> A;
-#define IX(j) (NEG ? N - 1 - (j) : (j))
-    const V z = O::zero();
-    const V three = O::splat(3.f), mone = O::splat(-1.f);
-    const V lo0 = l[IX(0)];
-    const V h0 = O::mul(f[IX(0)], w.ninvF);
-    V hprev = PERIODIC ? O::mul(f[IX(N - 1)], w.ninvF) : z;
-    V hcur = h0;
-    V pend = z, carry = z, t2first = z;
-    lF = z;
-    db = z;
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-        const V f0 = f[IX(j)];
-        const V hnext = (j + 1 < N) ? O::mul(f[IX(j + 1 < N ? j + 1 : 0)], w.ninvF)
-                                    : (PERIODIC ? h0 : z);
-        const V lo = j == 0 ? lo0 : l[IX(j)];
-        const V ln = (j + 1 < N) ? l[IX(j + 1 < N ? j + 1 : 0)] : (PERIODIC ? lo0 : z);
-        const V mu = O::sub(ln, lo);
-        const V u1 = O::fma(f0, w.r3, hnext);
-        const V u2 = O::fma(f0, w.r3, hprev);
-        const V s1 = A::fsat(f0, w.r3, hnext);
-        const V s2 = A::fsat(f0, w.r3, hprev);
-        const V i1 = A::eq(s1, u1), i2 = A::eq(s2, u2);
-        const V a = O::mul(w.c1, mu), b = O::mul(w.c2, mu);
-        const V t1 = O::mul(a, i1), t2 = O::mul(b, i2);
-        const V l0 = O::fma(w.K0, mu, O::mul(three, O::sub(t2, t1)));
-        if (j >= 1) l[IX(j >= 1 ? j - 1 : 0)] = O::sub(pend, t2);
-        else t2first = t2;
-        pend = O::add(O::add(lo, carry), l0);
-        carry = t1;
-        lF = O::fma(a, O::fma(u1, i1, O::mul(s1, mone)), lF);      // a (u1 I1 - s1)
-        lF = O::fma(b, O::fma(O::mul(u2, mone), i2, s2), lF);      // b (s2 - u2 I2)
-        if (DB) {
-            const V e = O::fma(w.Fd2, s2, O::fma(w.Fd1, s1, O::mul(w.kf, f0)));
-            db = O::fma(mu, e, db);
-        }
-        hprev = hcur;
-        hcur = hnext;
-    }
-    l[IX(N - 1)] = pend;
-    if (PERIODIC) {
-        l[IX(N - 1)] = O::sub(l[IX(N - 1)], t2first);
-        l[IX(0)] = O::add(l[IX(0)], carry);
-    }
-#undef IX
-}
+// One cell of the line adjoint (upwind position j).  In: the cell f0, the
+// scaled neighbours hprev, hnext, the output cotangents lo = l_j, ln =
+// l_{j+1}, the pending input cotangent pend of cell j - 1 and nm1p =
+// -m1_{j-1}.  With mu = ln - lo, nI = -[arm interior] and nm = mu nI:
+//   l^in_{j-1} = pend - c2 m2_j                         (returned in done)
+//   pend'      = lo + K0 mu - 3 c1 m1_j + 3 c2 m2_j + c1 m1_{j-1}
+// and the line sums G1 += mu g1, G2 += mu g2 with g = s + nI u, which is
+// exactly the indicator of the arm saturated at 1 (0 when interior, s when
+// saturated), so that l_F = c2 G2 - c1 G1.  DB: S1, S2, SF accumulate
+// mu s1, mu s2 and mu f.
+template <typename V, bool DB>
+struct AdjCell {
+    V pend, nm1p, G1, G2, S1, S2, SF;
 
-// As adjoint_line, with the output cotangent read from memory (lsrc, stride
-// ls elements of V) and the input cotangent written to memory (ldst, stride
-// ld; may equal lsrc: every element is read before it is overwritten).
-// Outflow boundaries (velocity lines).
-template <typename V, int N, bool NEG, bool DB>
-__device__ __forceinline__ void adjoint_line_mem(const V (&f)[N], const V *lsrc, int ls, V *ldst,
-                                                 int ld, const AdjW<V> &w, V &lF, V &db)
-{
-    typedef VOps<V> O;
-    typedef AOps<V> A;
-#define IX(j) (NEG ? N - 1 - (j) : (j))
-    const V z = O::zero();
-    const V three = O::splat(3.f), mone = O::splat(-1.f);
-    V hprev = z, hcur = O::mul(f[IX(0)], w.ninvF);
-    V pend = z, carry = z;
-    V lo = lsrc[IX(0) * ls];
-    lF = z;
-    db = z;
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-        const V f0 = f[IX(j)];
-        const V hnext = (j + 1 < N) ? O::mul(f[IX(j + 1 < N ? j + 1 : 0)], w.ninvF) : z;
-        const V ln = (j + 1 < N) ? lsrc[IX(j + 1 < N ? j + 1 : 0) * ls] : z;
+    __device__ __forceinline__ void init()
+    {
+        const V z = VOps<V>::zero();
+        pend = z; nm1p = z; G1 = z; G2 = z; S1 = z; S2 = z; SF = z;
+    }
+
+    template <bool FIRST>
+    __device__ __forceinline__ V step(V f0, V hprev, V hnext, V lo, V ln, const AdjW<V> &w, V &nm2)
+    {
+        typedef VOps<V> O;
+        typedef AOps<V> A;
         const V mu = O::sub(ln, lo);
         const V u1 = O::fma(f0, w.r3, hnext);
         const V u2 = O::fma(f0, w.r3, hprev);
         const V s1 = A::fsat(f0, w.r3, hnext);
         const V s2 = A::fsat(f0, w.r3, hprev);
-        const V i1 = A::eq(s1, u1), i2 = A::eq(s2, u2);
-        const V a = O::mul(w.c1, mu), b = O::mul(w.c2, mu);
-        const V t1 = O::mul(a, i1), t2 = O::mul(b, i2);
-        const V l0 = O::fma(w.K0, mu, O::mul(three, O::sub(t2, t1)));
-        if (j >= 1) ldst[IX(j >= 1 ? j - 1 : 0) * ld] = O::sub(pend, t2);
-        pend = O::add(O::add(lo, carry), l0);
-        carry = t1;
-        lF = O::fma(a, O::fma(u1, i1, O::mul(s1, mone)), lF);
-        lF = O::fma(b, O::fma(O::mul(u2, mone), i2, s2), lF);
+        const V nI1 = A::neq(s1, u1), nI2 = A::neq(s2, u2);
+        const V nm1 = O::mul(mu, nI1);
+        nm2 = O::mul(mu, nI2);
+        V x = O::fma(w.K0, mu, lo);
+        x = O::fma(w.c3a, nm1, x);
+        x = O::fma(w.c3b, nm2, x);
+        if (!FIRST) x = O::fma(w.nc1, nm1p, x);
+        const V done = O::fma(w.c2, nm2, pend);
+        pend = x;
+        nm1p = nm1;
+        G1 = O::fma(mu, O::fma(nI1, u1, s1), G1);
+        G2 = O::fma(mu, O::fma(nI2, u2, s2), G2);
         if (DB) {
-            const V e = O::fma(w.Fd2, s2, O::fma(w.Fd1, s1, O::mul(w.kf, f0)));
-            db = O::fma(mu, e, db);
+            S1 = O::fma(mu, s1, S1);
+            S2 = O::fma(mu, s2, S2);
+            SF = O::fma(mu, f0, SF);
+        }
+        return done;
+    }
+
+    __device__ __forceinline__ void finish(const AdjW<V> &w, V &lF, V &db) const
+    {
+        typedef VOps<V> O;
+        lF = O::fma(w.c2, G2, O::mul(w.nc1, G1));
+        db = DB ? O::fma(w.Fd2, S2, O::fma(w.Fd1, S1, O::mul(w.kf, SF))) : O::zero();
+    }
+};
+
+// Cotangent of the zero-shift update of one line in upwind order (lines with
+// u < 0 are passed mirrored), through accessors of compile-time position j:
+// fget(j) the state, lget(j) the output cotangent, lput(j, v) the input
+// cotangent (without the f_inf term: l_F is returned for the caller to
+// place).  Every state and cotangent element is read once, in increasing j,
+// before position j - 1 is written (at step j), so lput may write over the
+// storage of fget or lget; with PERIODIC, positions 0 and N - 1 are written
+// last.
+template <typename V, int N, bool PERIODIC, bool DB, class FG, class LG, class LP>
+__device__ __forceinline__ void adjoint_line_acc(FG fget, LG lget, LP lput, const AdjW<V> &w,
+                                                 V &lF, V &db)
+{
+    typedef VOps<V> O;
+    const V z = O::zero();
+    const V f0 = fget(0), l0 = lget(0);
+    const V h0 = O::mul(f0, w.ninvF);
+    V hprev = PERIODIC ? O::mul(fget(N - 1), w.ninvF) : z;
+    V fcur = f0, hcur = h0, lo = l0, nm2 = z, nm2first = z, first = z;
+    AdjCell<V, DB> c;
+    c.init();
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const V fnext = (j + 1 < N) ? fget(j + 1 < N ? j + 1 : 0) : z;
+        const V hnext = (j + 1 < N) ? O::mul(fnext, w.ninvF) : (PERIODIC ? h0 : z);
+        const V ln = (j + 1 < N) ? lget(j + 1 < N ? j + 1 : 0) : (PERIODIC ? l0 : z);
+        if (j == 0) {
+            c.template step<true>(fcur, hprev, hnext, lo, ln, w, nm2);
+            nm2first = nm2;
+        } else {
+            const V d = c.template step<false>(fcur, hprev, hnext, lo, ln, w, nm2);
+            if (PERIODIC && j == 1) first = d;
+            else lput(j - 1, d);
         }
         hprev = hcur;
         hcur = hnext;
         lo = ln;
+        fcur = fnext;
     }
-    ldst[IX(N - 1) * ld] = pend;
-#undef IX
+    if (PERIODIC) {
+        lput(N - 1, O::fma(w.c2, nm2first, c.pend));
+        lput(0, O::fma(w.nc1, c.nm1p, first));
+    } else {
+        lput(N - 1, c.pend);
+    }
+    c.finish(w, lF, db);
 }
 
-// first position in upwind order of the maximum m of the line v (array index)
+// the line in registers: l is overwritten with the input cotangent
+template <typename V, int N, bool PERIODIC, bool DB>
+__device__ __forceinline__ void adjoint_line(const V (&f)[N], V (&l)[N], const AdjW<V> &w, V &lF,
+                                             V &db)
+{
+    adjoint_line_acc<V, N, PERIODIC, DB>([&](int j) { return f[j]; }, [&](int j) { return l[j]; },
+                                         [&](int j, V v) { l[j] = v; }, w, lF, db);
+}
+
+// the state in registers, the cotangent in memory (lsrc, stride ls elements
+// of V; mirrored lines pass the last element and a negative stride) and the
+// input cotangent written to memory (ldst, stride ld; may equal lsrc)
+template <typename V, int N, bool PERIODIC, bool DB>
+__device__ __forceinline__ void adjoint_line_mem(const V (&f)[N], const V *lsrc, int ls, V *ldst,
+                                                 int ld, const AdjW<V> &w, V &lF, V &db)
+{
+    adjoint_line_acc<V, N, PERIODIC, DB>([&](int j) { return f[j]; },
+                                         [&](int j) { return lsrc[j * ls]; },
+                                         [&](int j, V v) { ldst[j * ld] = v; }, w, lF, db);
+}
+
+// first array position of the maximum m of the line v (lines in upwind order)
 template <int N>
-__device__ __forceinline__ int first_max(const float (&v)[N], float m, bool neg)
+__device__ __forceinline__ int first_max(const float (&v)[N], float m)
 {
     int a = 0;
-    if (!neg) {
 #pragma unroll
-        for (int j = N - 1; j >= 0; --j) a = v[j] == m ? j : a;
-    } else {
-#pragma unroll
-        for (int j = 0; j < N; ++j) a = v[j] == m ? j : a;
-    }
+    for (int j = N - 1; j >= 0; --j) a = v[j] == m ? j : a;
     return a;
 }
 
 template <int N>
-__device__ __forceinline__ int2 first_max2(const float2 (&x)[N], float2 m, bool neg)
+__device__ __forceinline__ int2 first_max2(const float2 (&x)[N], float2 m)
 {
     int ax = 0, ay = 0;
-    if (!neg) {
 #pragma unroll
-        for (int j = N - 1; j >= 0; --j) {
-            ax = x[j].x == m.x ? j : ax;
-            ay = x[j].y == m.y ? j : ay;
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            ax = x[j].x == m.x ? j : ax;
-            ay = x[j].y == m.y ? j : ay;
-        }
+    for (int j = N - 1; j >= 0; --j) {
+        ax = x[j].x == m.x ? j : ax;
+        ay = x[j].y == m.y ? j : ay;
     }
     return make_int2(ax, ay);
 }
 
-// one scalar line of a pair (component c) whose directions differ
-template <int N, bool PERIODIC>
+// one scalar line in upwind order: returns the beta derivative (in the
+// frame of the velocity axis), the upwind position of the line maximum and
+// its cotangent 2 l_F
+template <int N, bool PERIODIC, bool DB>
 __device__ __forceinline__ float adjoint_scalar(const float (&f)[N], float (&l)[N],
-                                                const LineCoef<float> &cf, bool db_on,
-                                                int &arg, float &lfinf)
+                                                const LineCoef<float> &cf, int &arg, float &lfinf)
 {
     const float finf = line_max(f);
+    arg = first_max<N>(f, finf);
     const AdjW<float> w = adj_weights(cf, finf);
     float lF, db;
-    if (cf.code & 1) {
-        if (db_on) adjoint_line<float, N, PERIODIC, true, true>(f, l, w, lF, db);
-        else adjoint_line<float, N, PERIODIC, true, false>(f, l, w, lF, db);
-    } else {
-        if (db_on) adjoint_line<float, N, PERIODIC, false, true>(f, l, w, lF, db);
-        else adjoint_line<float, N, PERIODIC, false, false>(f, l, w, lF, db);
-    }
-    arg = first_max<N>(f, finf, cf.code & 1);
+    adjoint_line<float, N, PERIODIC, DB>(f, l, w, lF, db);
     lfinf = 2.f * lF;
     return (cf.code & 1) ? -db : db;
 }
 
 // a pair of lines travelling in opposite directions: two scalar adjoints,
-// out of line (the arrays are copies in local memory; rare)
+// out of line (the arrays are copies in local memory, each put in upwind
+// order; rare).  f, l in array order; arg returns array positions.
 template <int N, bool PERIODIC, bool DB>
 __device__ __noinline__ float adjoint_pair_mixed(const float2 *f, float2 *l, LineCoef<float> ca,
                                                  LineCoef<float> cb, int *arg, float *lfinf)
 {
     float fx[N], fy[N], lx[N], ly[N];
+    const bool nx = ca.code & 1, ny = cb.code & 1;
     for (int j = 0; j < N; ++j) {
-        fx[j] = f[j].x; fy[j] = f[j].y;
-        lx[j] = l[j].x; ly[j] = l[j].y;
+        const int jx = nx ? N - 1 - j : j, jy = ny ? N - 1 - j : j;
+        fx[j] = f[jx].x; fy[j] = f[jy].y;
+        lx[j] = l[jx].x; ly[j] = l[jy].y;
     }
-    const float dx = adjoint_scalar<N, PERIODIC>(fx, lx, ca, DB, arg[0], lfinf[0]);
-    const float dy = adjoint_scalar<N, PERIODIC>(fy, ly, cb, DB, arg[1], lfinf[1]);
-    for (int j = 0; j < N; ++j) l[j] = make_float2(lx[j], ly[j]);
+    const float dx = adjoint_scalar<N, PERIODIC, DB>(fx, lx, ca, arg[0], lfinf[0]);
+    const float dy = adjoint_scalar<N, PERIODIC, DB>(fy, ly, cb, arg[1], lfinf[1]);
+    for (int j = 0; j < N; ++j) {
+        const int jx = nx ? N - 1 - j : j, jy = ny ? N - 1 - j : j;
+        l[jx].x = lx[j];
+        l[jy].y = ly[j];
+    }
+    if (nx) arg[0] = N - 1 - arg[0];
+    if (ny) arg[1] = N - 1 - arg[1];
     return dx + dy;
 }
 
@@ -381,30 +390,36 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(const float *__restrict__
             atomicExch(skipped, 1);
             continue;
         }
+        // lines of one direction are loaded in upwind order (u < 0: from the
+        // far end with a negative stride); a mixed pair in array order
+        const bool same = !MIXED || (ca.code & 1) == (cb.code & 1);
+        const bool neg = same && (ca.code & 1);
+        const long long st = neg ? -stride : stride;
+        const long long o0 = neg ? off + (N - 1) * stride : off;
         float2 f[N], l[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-            f[j] = *reinterpret_cast<const float2 *>(fin + off + j * stride);
-            l[j] = *reinterpret_cast<const float2 *>(lam + off + j * stride);
+            f[j] = *reinterpret_cast<const float2 *>(fin + o0 + j * st);
+            l[j] = *reinterpret_cast<const float2 *>(lam + o0 + j * st);
         }
         if constexpr (BC) {
+            const float *sb = sbc + (neg ? N - 1 : 0);
+            const int ss = neg ? -1 : 1;
 #pragma unroll
             for (int j = 0; j < N; ++j) {
-                const float b = sbc[j];
+                const float b = sb[j * ss];
                 l[j].x += b;
                 l[j].y += b;
             }
         }
         int ax, ay;
         float lfx, lfy;
-        if (!MIXED || (ca.code & 1) == (cb.code & 1)) {
+        if (same) {
             const float2 finf = line_max(f);
             const AdjW<float2> w = adj_weights(ca, cb, finf);
             float2 lF, db;
-            const bool neg = ca.code & 1;
-            if (neg) adjoint_line<float2, N, PERIODIC, true, DB>(f, l, w, lF, db);
-            else adjoint_line<float2, N, PERIODIC, false, DB>(f, l, w, lF, db);
-            const int2 a2 = first_max2<N>(f, finf, neg);
+            adjoint_line<float2, N, PERIODIC, DB>(f, l, w, lF, db);
+            const int2 a2 = first_max2<N>(f, finf);
             ax = a2.x;
             ay = a2.y;
             lfx = 2.f * lF.x;
@@ -424,14 +439,76 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(const float *__restrict__
             for (int j = 0; j < N; ++j) l[j] = lm[j];
         }
 #pragma unroll
-        for (int j = 0; j < N; ++j) *reinterpret_cast<float2 *>(lam + off + j * stride) = l[j];
-        lam[off + ax * stride] += lfx;
-        lam[off + ay * stride + 1] += lfy;
+        for (int j = 0; j < N; ++j) *reinterpret_cast<float2 *>(lam + o0 + j * st) = l[j];
+        lam[o0 + ax * st] += lfx;
+        lam[o0 + ay * st + 1] += lfy;
     }
     if (DB) {
         const double s = block_sum((double)da, red);
         if (t == 0 && s != 0.0) atomicAdd(lam_g + blockIdx.y, s * scale);
     }
+}
+
+// 32 contiguous rows of N floats (global) to a tile of pitch P and back,
+// each row reversed when rev (warp-uniform): a row of a line with u < 0 is
+// held in upwind order
+template <int N, int P>
+__device__ __forceinline__ void rows_in(float *tile, const float *g, bool rev, int lane)
+{
+    constexpr int Q = N / 4;
+    if (!rev) {
+#pragma unroll 4
+        for (int e = lane; e < 32 * Q; e += 32) {
+            const int r = e / Q, c = 4 * (e % Q);
+            *reinterpret_cast<float4 *>(tile + r * P + c) = *reinterpret_cast<const float4 *>(g + r * N + c);
+        }
+    } else {
+#pragma unroll 4
+        for (int e = lane; e < 32 * Q; e += 32) {
+            const int r = e / Q, c = 4 * (e % Q);
+            const float4 v = *reinterpret_cast<const float4 *>(g + r * N + c);
+            *reinterpret_cast<float4 *>(tile + r * P + (N - 4 - c)) = make_float4(v.w, v.z, v.y, v.x);
+        }
+    }
+}
+
+template <int N, int P>
+__device__ __forceinline__ void rows_out(float *g, const float *tile, bool rev, int lane)
+{
+    constexpr int Q = N / 4;
+    if (!rev) {
+#pragma unroll 4
+        for (int e = lane; e < 32 * Q; e += 32) {
+            const int r = e / Q, c = 4 * (e % Q);
+            *reinterpret_cast<float4 *>(g + r * N + c) = *reinterpret_cast<const float4 *>(tile + r * P + c);
+        }
+    } else {
+#pragma unroll 4
+        for (int e = lane; e < 32 * Q; e += 32) {
+            const int r = e / Q, c = 4 * (e % Q);
+            const float4 v = *reinterpret_cast<const float4 *>(tile + r * P + (N - 4 - c));
+            *reinterpret_cast<float4 *>(g + r * N + c) = make_float4(v.w, v.z, v.y, v.x);
+        }
+    }
+}
+
+// one row of the tile (pitch P) to registers and back
+template <int N>
+__device__ __forceinline__ void row_load(float (&x)[N], const float *row)
+{
+#pragma unroll
+    for (int c = 0; c < N; c += 4) {
+        const float4 a = *reinterpret_cast<const float4 *>(row + c);
+        x[c] = a.x; x[c + 1] = a.y; x[c + 2] = a.z; x[c + 3] = a.w;
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void row_store(float *row, const float (&x)[N])
+{
+#pragma unroll
+    for (int c = 0; c < N; c += 4)
+        *reinterpret_cast<float4 *>(row + c) = make_float4(x[c], x[c + 1], x[c + 2], x[c + 3]);
 }
 
 // vz sweep of FP32 cubes of edge N (16 or 32): warp units of 32 rows
@@ -442,7 +519,7 @@ __global__ void __launch_bounds__(128) k_adjoint_rows(const float *__restrict__ 
                                                      long long np, double *__restrict__ lam_g,
                                                      double scale, int *skipped)
 {
-    constexpr int P = N + 4, Q = N / 4, UPC = N * N / 32;   // pitch, chunks per row, units per cube
+    constexpr int P = N + 4, UPC = N * N / 32;   // pitch, units per cube
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *tf = reinterpret_cast<float *>(smem_raw) + warp * 2 * 32 * P;
@@ -455,35 +532,21 @@ __global__ void __launch_bounds__(128) k_adjoint_rows(const float *__restrict__ 
         if (lane == 0) atomicExch(skipped, 1);
         return;
     }
+    const bool neg = cf.code & 1;
     const long long off = unit * 32 * N;          // 32 contiguous rows
-#pragma unroll
-    for (int e = lane; e < 32 * Q; e += 32) {
-        const int r = e / Q, c = 4 * (e % Q);
-        *reinterpret_cast<float4 *>(tf + r * P + c) = *reinterpret_cast<const float4 *>(fin + off + r * N + c);
-        *reinterpret_cast<float4 *>(tl + r * P + c) = *reinterpret_cast<const float4 *>(lam + off + r * N + c);
-    }
+    rows_in<N, P>(tf, fin + off, neg, lane);
+    rows_in<N, P>(tl, lam + off, neg, lane);
     __syncwarp();
     float f[N], l[N];
-#pragma unroll
-    for (int c = 0; c < N; c += 4) {
-        const float4 a = *reinterpret_cast<const float4 *>(tf + lane * P + c);
-        const float4 b = *reinterpret_cast<const float4 *>(tl + lane * P + c);
-        f[c] = a.x; f[c + 1] = a.y; f[c + 2] = a.z; f[c + 3] = a.w;
-        l[c] = b.x; l[c + 1] = b.y; l[c + 2] = b.z; l[c + 3] = b.w;
-    }
+    row_load<N>(f, tf + lane * P);
+    row_load<N>(l, tl + lane * P);
     int arg;
     float lfinf;
-    const float db = adjoint_scalar<N, false>(f, l, cf, true, arg, lfinf);
-#pragma unroll
-    for (int c = 0; c < N; c += 4)
-        *reinterpret_cast<float4 *>(tl + lane * P + c) = make_float4(l[c], l[c + 1], l[c + 2], l[c + 3]);
+    const float db = adjoint_scalar<N, false, true>(f, l, cf, arg, lfinf);
+    row_store<N>(tl + lane * P, l);
     tl[lane * P + arg] += lfinf;
     __syncwarp();
-#pragma unroll
-    for (int e = lane; e < 32 * Q; e += 32) {
-        const int r = e / Q, c = 4 * (e % Q);
-        *reinterpret_cast<float4 *>(lam + off + r * N + c) = *reinterpret_cast<const float4 *>(tl + r * P + c);
-    }
+    rows_out<N, P>(lam + off, tl, neg, lane);
     if (!lam_g) return;
     float s = db;
     for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
@@ -514,7 +577,7 @@ __global__ void __launch_bounds__(128) k_kick_adjoint_zy(const float *__restrict
                                                         double scale_y, double scale_z,
                                                         int *skipped)
 {
-    constexpr int P = KickZY<N>::P, Q = KickZY<N>::Q, UPC = KickZY<N>::UPC;
+    constexpr int P = KickZY<N>::P, UPC = KickZY<N>::UPC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *tl = reinterpret_cast<float *>(smem_raw) + warp * 3 * 32 * P;
@@ -529,15 +592,13 @@ __global__ void __launch_bounds__(128) k_kick_adjoint_zy(const float *__restrict
         return;
     }
     const long long off = unit * 32 * N;
-#pragma unroll 4
-    for (int e = lane; e < 32 * Q; e += 32) {
-        const int r = e / Q, c = 4 * (e % Q);
-        *reinterpret_cast<float4 *>(tl + r * P + c) = *reinterpret_cast<const float4 *>(lam + off + r * N + c);
-        *reinterpret_cast<float4 *>(tb + r * P + c) = *reinterpret_cast<const float4 *>(sb + off + r * N + c);
-    }
+    const bool negy = cy.code & 1, negz = cz.code & 1;
+    // the cotangent rows in upwind order along vz; the vy input as it is
+    rows_in<N, P>(tl, lam + off, negz, lane);
+    rows_in<N, P>(tb, sb + off, false, lane);
     __syncwarp();
     const int pl = lane / N, k = lane % N;          // this lane's vy column
-    const bool negy = cy.code & 1;
+    const int kt = negz ? N - 1 - k : k;            // its position in the upwind rows
     {
         float x[N];
 #pragma unroll
@@ -545,47 +606,39 @@ __global__ void __launch_bounds__(128) k_kick_adjoint_zy(const float *__restrict
         const LineW<float> w = weights_one<float>(cy, line_max(x));
         update_line<float, N, false>(x, w, negy);
 #pragma unroll
-        for (int j = 0; j < N; ++j) tc[(pl * N + j) * P + k] = x[j];
+        for (int j = 0; j < N; ++j) tc[(pl * N + j) * P + kt] = x[j];
     }
     __syncwarp();
     float dz, dy;
     {
         float f[N], l[N];
-#pragma unroll
-        for (int c = 0; c < N; c += 4) {
-            const float4 a = *reinterpret_cast<const float4 *>(tc + lane * P + c);
-            const float4 b = *reinterpret_cast<const float4 *>(tl + lane * P + c);
-            f[c] = a.x; f[c + 1] = a.y; f[c + 2] = a.z; f[c + 3] = a.w;
-            l[c] = b.x; l[c + 1] = b.y; l[c + 2] = b.z; l[c + 3] = b.w;
-        }
+        row_load<N>(f, tc + lane * P);
+        row_load<N>(l, tl + lane * P);
         int arg;
         float lfinf;
-        dz = adjoint_scalar<N, false>(f, l, cz, true, arg, lfinf);
-#pragma unroll
-        for (int c = 0; c < N; c += 4)
-            *reinterpret_cast<float4 *>(tl + lane * P + c) = make_float4(l[c], l[c + 1], l[c + 2], l[c + 3]);
+        dz = adjoint_scalar<N, false, true>(f, l, cz, arg, lfinf);
+        row_store<N>(tl + lane * P, l);
         tl[lane * P + arg] += lfinf;
     }
     __syncwarp();
     {
+        // the vy column in upwind order (u < 0: from the last row up)
+        const int r0 = negy ? N - 1 : 0, rs = negy ? -P : P;
+        const float *B = tb + (pl * N + r0) * P + k;
         float f[N];
 #pragma unroll
-        for (int j = 0; j < N; ++j) f[j] = tb[(pl * N + j) * P + k];
+        for (int j = 0; j < N; ++j) f[j] = B[j * rs];
         const float finf = line_max(f);
+        const int arg = first_max<N>(f, finf);
         const AdjW<float> w = adj_weights(cy, finf);
-        float *L = tl + pl * N * P + k;
+        float *L = tl + (pl * N + r0) * P + kt;
         float lF, db;
-        if (negy) adjoint_line_mem<float, N, true, true>(f, L, P, L, P, w, lF, db);
-        else adjoint_line_mem<float, N, false, true>(f, L, P, L, P, w, lF, db);
-        L[first_max<N>(f, finf, negy) * P] += 2.f * lF;
+        adjoint_line_mem<float, N, false, true>(f, L, rs, L, rs, w, lF, db);
+        L[arg * rs] += 2.f * lF;
         dy = negy ? -db : db;
     }
     __syncwarp();
-#pragma unroll 4
-    for (int e = lane; e < 32 * Q; e += 32) {
-        const int r = e / Q, c = 4 * (e % Q);
-        *reinterpret_cast<float4 *>(lam + off + r * N + c) = *reinterpret_cast<const float4 *>(tl + r * P + c);
-    }
+    rows_out<N, P>(lam + off, tl, negz, lane);
     if (!lam_g) return;
     for (int d = 16; d > 0; d >>= 1) {
         dz += __shfl_xor_sync(0xffffffffu, dz, d);
@@ -599,13 +652,17 @@ __global__ void __launch_bounds__(128) k_kick_adjoint_zy(const float *__restrict
 
 // The y and then the z drift adjoint in one pass (FP32, N_y = N_z = N, 16
 // (N = 32) or 32 (N = 16) velocity cells per CTA, zero-shift drifts), the
-// transpose of k_drift_yz: the y adjoint reads its lines (pairs of adjacent
-// velocity cells) of the cotangent and of the y input straight from global
-// memory and writes the result to a shared tile [y][z][VC]; the z adjoint
-// reads its cotangent lines from the tile and the z input from global memory
-// and writes the result back.  The cotangent crosses HBM once for the two
-// sweeps.  Pairs of z lines with directions of both signs go through the
-// scalar path.
+// transpose of k_drift_yz.  The y input is not stored: the CTA recomputes it
+// from the z input s3 (the z sweep of its lines, bitwise as the forward pass)
+// into a shared tile [y][z][VC].  The y adjoint (lines of two adjacent
+// velocity cells) holds its cotangent line, read from global memory, in
+// registers and streams the state from the tile, writing the result over it
+// (each thread reads and writes only its own line); the z adjoint holds the
+// z input, read again from global memory (the CTA's 64 KB of s3 are still in
+// L2), in registers and streams its cotangent from the tile, writing the
+// result to global memory.  One line array per thread keeps two CTAs per SM.
+// The cotangent crosses HBM once for the two sweeps.  Pairs of z lines with
+// directions of both signs go through the scalar path.
 template <int N>
 struct AdjYZ {
     static constexpr int VC = 512 / N, NT = N * VC / 2;
@@ -613,82 +670,111 @@ struct AdjYZ {
     static constexpr size_t SMEM = (size_t)N * YP * sizeof(float);
 };
 
+// maximum (at least 0) and its first position of a line read through fget
+template <int N, class FG>
+__device__ __forceinline__ float2 scan_max2(FG fget, int2 &arg)
+{
+    float2 m = make_float2(0.f, 0.f);
+    int ax = 0, ay = 0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const float2 v = fget(j);
+        ax = v.x > m.x ? j : ax;
+        ay = v.y > m.y ? j : ay;
+        m.x = fmaxf(m.x, v.x);
+        m.y = fmaxf(m.y, v.y);
+    }
+    arg = make_int2(ax, ay);
+    return m;
+}
+
 template <int N, bool PERIODIC>
-__global__ void __launch_bounds__(AdjYZ<N>::NT, 1) k_drift_adjoint_yz(
-    const float *__restrict__ s4, const float *__restrict__ s3, float *__restrict__ lam,
-    const LineCoef<float> *__restrict__ cz, const LineCoef<float> *__restrict__ cy, long long nvc,
-    int nvy, int nvz)
+__global__ void __launch_bounds__(AdjYZ<N>::NT, 2) k_drift_adjoint_yz(
+    const float *__restrict__ s3, float *__restrict__ lam, const LineCoef<float> *__restrict__ cz,
+    const LineCoef<float> *__restrict__ cy, long long nvc, int nvy, int nvz)
 {
     constexpr int VC = AdjYZ<N>::VC, YP = AdjYZ<N>::YP, H = VC / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *tile = reinterpret_cast<float *>(smem_raw);
-    const int t = threadIdx.x, vp = t % H, r = t / H;    // r: z in the y adjoint, y in the z adjoint
+    const int t = threadIdx.x, vp = t % H, r = t / H;    // r: y in the z sweeps, z in the y adjoint
     const long long v0 = (long long)blockIdx.x * VC;
     const long long x0 = (long long)blockIdx.y * N * N;
     const long long v = v0 + 2 * vp;
+    const LineCoef<float> ca = cz[(int)(v % nvz)], cb = cz[(int)((v + 1) % nvz)];
+    const long long zoff = (x0 + (long long)r * N) * nvc + v;   // z line (y = r, v pair)
     {
-        // y adjoint: line (z = r, v pair), cells y = 0..N-1
-        const long long off = (x0 + r) * nvc + v;
-        float2 f[N], l[N];
+        // the y input: the forward z sweep of the line (y = r, v pair)
+        float2 x[N];
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-            f[j] = *reinterpret_cast<const float2 *>(s4 + off + (long long)j * N * nvc);
-            l[j] = *reinterpret_cast<const float2 *>(lam + off + (long long)j * N * nvc);
-        }
+        for (int j = 0; j < N; ++j) x[j] = *reinterpret_cast<const float2 *>(s3 + zoff + j * nvc);
+        drift_pair<N, PERIODIC>(x, ca, cb);
+        float *q = tile + r * YP + 2 * vp;
+#pragma unroll
+        for (int j = 0; j < N; ++j) *reinterpret_cast<float2 *>(q + j * VC) = x[j];
+    }
+    __syncthreads();
+    {
+        // y adjoint: line (z = r, v pair), cells y = 0..N-1 in upwind order
         const LineCoef<float> c = cy[(int)((v0 / nvz) % nvy)];
-        const float2 finf = line_max(f);
+        const bool neg = c.code & 1;
+        const long long st = neg ? -(long long)N * nvc : (long long)N * nvc;
+        const long long o0 = (x0 + r) * nvc + v + (neg ? (N - 1) * (long long)N * nvc : 0);
+        const int ys = neg ? -YP : YP;
+        float2 *q = reinterpret_cast<float2 *>(tile + r * VC + 2 * vp + (neg ? (N - 1) * YP : 0));
+        const int qs = ys / 2;
+        float2 l[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) l[j] = *reinterpret_cast<const float2 *>(lam + o0 + j * st);
+        int2 am;
+        const float2 finf = scan_max2<N>([&](int j) { return q[j * qs]; }, am);
         const AdjW<float2> w = adj_weights(c, c, finf);
         float2 lF, db;
-        const bool neg = c.code & 1;
-        if (neg) adjoint_line<float2, N, PERIODIC, true, false>(f, l, w, lF, db);
-        else adjoint_line<float2, N, PERIODIC, false, false>(f, l, w, lF, db);
-        const int2 am = first_max2<N>(f, finf, neg);
-        float *q = tile + r * VC + 2 * vp;              // tile [y][z][vc]
-#pragma unroll
-        for (int j = 0; j < N; ++j) *reinterpret_cast<float2 *>(q + j * YP) = l[j];
-        q[am.x * YP] += 2.f * lF.x;
-        q[am.y * YP + 1] += 2.f * lF.y;
+        adjoint_line_acc<float2, N, PERIODIC, false>(
+            [&](int j) { return q[j * qs]; }, [&](int j) { return l[j]; },
+            [&](int j, float2 u) { q[j * qs] = u; }, w, lF, db);
+        float *qf = reinterpret_cast<float *>(q);
+        qf[am.x * ys] += 2.f * lF.x;
+        qf[am.y * ys + 1] += 2.f * lF.y;
     }
     __syncthreads();
     {
         // z adjoint: line (y = r, v pair), cells z = 0..N-1
-        const long long off = (x0 + (long long)r * N) * nvc + v;
-        float2 f[N], l[N];
-        const float *q = tile + r * YP + 2 * vp;
+        const bool same = (ca.code & 1) == (cb.code & 1);
+        const bool neg = same && (ca.code & 1);
+        const long long st = neg ? -(long long)nvc : (long long)nvc;
+        const long long o0 = zoff + (neg ? (N - 1) * (long long)nvc : 0);
+        const int ts = neg ? -VC / 2 : VC / 2;
+        const float2 *q = reinterpret_cast<const float2 *>(tile + r * YP + 2 * vp + (neg ? (N - 1) * VC : 0));
+        float2 f[N];
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-            f[j] = *reinterpret_cast<const float2 *>(s3 + off + (long long)j * nvc);
-            l[j] = *reinterpret_cast<const float2 *>(q + j * VC);
-        }
-        const LineCoef<float> ca = cz[(int)(v % nvz)], cb = cz[(int)((v + 1) % nvz)];
+        for (int j = 0; j < N; ++j) f[j] = *reinterpret_cast<const float2 *>(s3 + o0 + j * st);
+        float2 *out = reinterpret_cast<float2 *>(lam + o0);
         int ax, ay;
         float lfx, lfy;
-        if ((ca.code & 1) == (cb.code & 1)) {
+        if (same) {
             const float2 finf = line_max(f);
+            const int2 am = first_max2<N>(f, finf);
             const AdjW<float2> w = adj_weights(ca, cb, finf);
             float2 lF, db;
-            const bool neg = ca.code & 1;
-            if (neg) adjoint_line<float2, N, PERIODIC, true, false>(f, l, w, lF, db);
-            else adjoint_line<float2, N, PERIODIC, false, false>(f, l, w, lF, db);
-            const int2 am = first_max2<N>(f, finf, neg);
+            adjoint_line_acc<float2, N, PERIODIC, false>(
+                [&](int j) { return f[j]; }, [&](int j) { return q[j * ts]; },
+                [&](int j, float2 u) { out[j * st / 2] = u; }, w, lF, db);
             ax = am.x; ay = am.y;
             lfx = 2.f * lF.x; lfy = 2.f * lF.y;
         } else {
             float2 fm[N], lm[N];
 #pragma unroll
-            for (int j = 0; j < N; ++j) { fm[j] = f[j]; lm[j] = l[j]; }
+            for (int j = 0; j < N; ++j) { fm[j] = f[j]; lm[j] = q[j * ts]; }
             int am[2];
             float lfm[2];
             adjoint_pair_mixed<N, PERIODIC, false>(fm, lm, ca, cb, am, lfm);
             ax = am[0]; ay = am[1];
             lfx = lfm[0]; lfy = lfm[1];
 #pragma unroll
-            for (int j = 0; j < N; ++j) l[j] = lm[j];
+            for (int j = 0; j < N; ++j) out[j * st / 2] = lm[j];
         }
-#pragma unroll
-        for (int j = 0; j < N; ++j) *reinterpret_cast<float2 *>(lam + off + (long long)j * nvc) = l[j];
-        lam[off + (long long)ax * nvc] += lfx;
-        lam[off + (long long)ay * nvc + 1] += lfy;
+        lam[o0 + ax * st] += lfx;
+        lam[o0 + ay * st + 1] += lfy;
     }
 }
 
@@ -767,20 +853,16 @@ cudaError_t launch_kick_adjoint3(vp_ctx *c, const void *sa, const void *sb, void
 
 // the y then z drift adjoints in one pass (zero-shift drifts: the caller
 // checks the shift bound); s4, s3 the inputs of the y and z drifts
-int vp_drift_adjoint_yz_ok(const vp_ctx *c)
-{
-    if (c->isdouble || c->n[1] != c->n[2]) return 0;
-    const int n = c->n[1];
-    if (n != 16 && n != 32) return 0;
-    return c->nv[2] % (512 / n) == 0 && c->n[0] <= 65535;
-}
+int vp_drift_adjoint_yz_ok(const vp_ctx *c) { return vp_drift_yz_ok(c); }
 
-cudaError_t launch_drift_adjoint_yz(vp_ctx *c, const void *s4, const void *s3, void *lam,
-                                    const void *coef)
+// the y then z drift adjoints in one pass (zero-shift drifts: the caller
+// checks the shift bound); s3 the input of the z drift (the input of the y
+// drift is recomputed from it)
+cudaError_t launch_drift_adjoint_yz(vp_ctx *c, const void *s3, void *lam, const void *coef)
 {
     const LineCoef<float> *cf = (const LineCoef<float> *)coef;
     const LineCoef<float> *cz = cf + (size_t)2 * c->maxnv, *cy = cf + (size_t)c->maxnv;
-    const float *a = (const float *)s4, *b = (const float *)s3;
+    const float *b = (const float *)s3;
     float *l = (float *)lam;
     cudaError_t e;
     if (c->n[1] == 32) {
@@ -790,15 +872,12 @@ cudaError_t launch_drift_adjoint_yz(vp_ctx *c, const void *s4, const void *s3, v
         if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM)) !=
             cudaSuccess)
             return e;
-        k<<<grid, K::NT, K::SMEM, c->stream>>>(a, b, l, cz, cy, c->nvc, c->nv[1], c->nv[2]);
+        k<<<grid, K::NT, K::SMEM, c->stream>>>(b, l, cz, cy, c->nvc, c->nv[1], c->nv[2]);
     } else {
         typedef AdjYZ<16> K;
         const dim3 grid((unsigned)(c->nvc / K::VC), (unsigned)c->n[0]);
         auto k = c->periodic_space ? k_drift_adjoint_yz<16, true> : k_drift_adjoint_yz<16, false>;
-        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM)) !=
-            cudaSuccess)
-            return e;
-        k<<<grid, K::NT, K::SMEM, c->stream>>>(a, b, l, cz, cy, c->nvc, c->nv[1], c->nv[2]);
+        k<<<grid, K::NT, K::SMEM, c->stream>>>(b, l, cz, cy, c->nvc, c->nv[1], c->nv[2]);
     }
     return cudaGetLastError();
 }

@@ -180,10 +180,10 @@ int vp_adjoint_pairs_ok(const vp_ctx *c, int axis);
 // are skipped and set c->adj_flag
 int vp_kick_adjoint3_ok(const vp_ctx *c);
 // the y then z drift adjoints of a zero-shift step in one pass (FP32,
-// N_y = N_z in {16, 32}); s4, s3: the inputs of the y and z drifts
+// N_y = N_z in {16, 32}); s3: the input of the z drift (the input of the y
+// drift is recomputed from it); the same grids as launch_drift_yz
 int vp_drift_adjoint_yz_ok(const vp_ctx *c);
-cudaError_t launch_drift_adjoint_yz(vp_ctx *c, const void *s4, const void *s3, void *lam,
-                                    const void *coef);
+cudaError_t launch_drift_adjoint_yz(vp_ctx *c, const void *s3, void *lam, const void *coef);
 cudaError_t launch_kick_adjoint3(vp_ctx *c, const void *sa, const void *sb, void *lam,
                                  const void *coef, double *lam_g, double tau);
 // cube3 (kick axes): skip every cube with a shift on any velocity axis and

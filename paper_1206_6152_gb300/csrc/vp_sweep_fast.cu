@@ -19,6 +19,7 @@
 
 #include "vp_device.cuh"
 #include "vp_internal.cuh"
+#include "vp_fast_line.cuh"
 #include "vp_line.cuh"
 
 using namespace vpline;
@@ -63,32 +64,6 @@ __device__ __noinline__ T kick_line_shifted(T *L, int st, int n, const LineCoef<
         ph = phm;
     }
     return lost;
-}
-
-__device__ __forceinline__ LineW<float2> weights_pair(const LineCoef<float> &cf, float2 finf)
-{
-    LineW<float2> w;
-    const int neg = cf.code & 1;
-    weights1<float>(cf.c0, cf.c1, cf.c2, neg, finf.x, w.K0.x, w.A1.x, w.A2.x, w.ninvF.x);
-    weights1<float>(cf.c0, cf.c1, cf.c2, neg, finf.y, w.K0.y, w.A1.y, w.A2.y, w.ninvF.y);
-    return w;
-}
-
-__device__ __forceinline__ LineW<float2> weights_pair2(const LineCoef<float> &ca,
-                                                        const LineCoef<float> &cb, float2 finf)
-{
-    LineW<float2> w;
-    weights1<float>(ca.c0, ca.c1, ca.c2, ca.code & 1, finf.x, w.K0.x, w.A1.x, w.A2.x, w.ninvF.x);
-    weights1<float>(cb.c0, cb.c1, cb.c2, cb.code & 1, finf.y, w.K0.y, w.A1.y, w.A2.y, w.ninvF.y);
-    return w;
-}
-
-template <typename S>
-__device__ __forceinline__ LineW<S> weights_one(const LineCoef<S> &cf, S finf)
-{
-    LineW<S> w;
-    weights1<S>(cf.c0, cf.c1, cf.c2, cf.code & 1, finf, w.K0, w.A1, w.A2, w.ninvF);
-    return w;
 }
 
 // ---------------------------------------------------------------------------
@@ -673,27 +648,6 @@ struct DriftYZ {
     static constexpr int NT = N * VC / 2;              // threads: one line pair each
     static constexpr int YP = N * VC + (VC == 16 ? 16 : 0);   // tile pitch of one y
 };
-
-template <int N, bool PERIODIC>
-__device__ __forceinline__ float drift_pair(float2 (&x)[N], const LineCoef<float> &ca,
-                                            const LineCoef<float> &cb)
-{
-    if ((ca.code & 1) == (cb.code & 1)) {
-        const LineW<float2> w = weights_pair2(ca, cb, line_max(x));
-        const float2 out = update_line<float2, N, PERIODIC>(x, w, ca.code & 1);
-        return out.x + out.y;
-    }
-    float y0[N], y1[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) { y0[j] = x[j].x; y1[j] = x[j].y; }
-    const LineW<float> w0 = weights_one<float>(ca, line_max(y0));
-    const LineW<float> w1 = weights_one<float>(cb, line_max(y1));
-    float lost = update_line<float, N, PERIODIC>(y0, w0, ca.code & 1);
-    lost += update_line<float, N, PERIODIC>(y1, w1, cb.code & 1);
-#pragma unroll
-    for (int j = 0; j < N; ++j) x[j] = make_float2(y0[j], y1[j]);
-    return lost;
-}
 
 template <int N, bool PERIODIC>
 __global__ void __launch_bounds__(DriftYZ<N>::NT) k_drift_yz(const float *__restrict__ f,
