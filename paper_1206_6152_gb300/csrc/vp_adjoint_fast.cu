@@ -308,6 +308,15 @@ __device__ __noinline__ float adjoint_pair_mixed(const float2 *f, float2 *l, Lin
     return dx + dy;
 }
 
+// asynchronous 8-byte copy global -> shared (no register staging) and the
+// wait for all of the thread's copies
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 struct PairGeom {
     int axis;                  // 0..5
     long long nvc;
@@ -329,9 +338,13 @@ struct PairGeom {
 // DB: the velocity sweeps' beta derivative; BC: add dvol_v lam_rho[cell] to
 // the cotangent on load (the density broadcast of the field adjoint)
 // MIXED: the two lines of a pair may travel in opposite directions (z drift,
-// where they differ in v_z); then they are done as two scalar lines
+// where they differ in v_z); then they are done as two scalar lines.
+// The state pair line is held in registers; the cotangent pair line is
+// copied asynchronously into the thread's own shared-memory slots (element j
+// of thread t at j * 128 + t: conflict-free) and streamed from there, which
+// keeps the kernel at 128 registers (16 warps per SM).
 template <int N, bool PERIODIC, bool DB, bool BC, bool MIXED>
-__global__ void __launch_bounds__(128) k_adjoint_pairs(const float *__restrict__ fin,
+__global__ void __launch_bounds__(128, 4) k_adjoint_pairs(const float *__restrict__ fin,
                                                       float *__restrict__ lam,
                                                       const LineCoef<float> *__restrict__ coef,
                                                       PairGeom g, const double *__restrict__ bc,
@@ -340,7 +353,9 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(const float *__restrict__
 {
     __shared__ double red[32];
     __shared__ float sbc[BC ? N : 1];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int t = threadIdx.x;
+    float2 *sl = reinterpret_cast<float2 *>(smem_raw) + t;     // slot j: sl[j * 128]
     long long base, u0, u1, stride, cell0 = 0;
     if (g.axis < 3) {
         const int o = blockIdx.y;
@@ -390,36 +405,39 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(const float *__restrict__
             atomicExch(skipped, 1);
             continue;
         }
-        // lines of one direction are loaded in upwind order (u < 0: from the
+        // lines of one direction are read in upwind order (u < 0: from the
         // far end with a negative stride); a mixed pair in array order
         const bool same = !MIXED || (ca.code & 1) == (cb.code & 1);
         const bool neg = same && (ca.code & 1);
         const long long st = neg ? -stride : stride;
         const long long o0 = neg ? off + (N - 1) * stride : off;
-        float2 f[N], l[N];
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-            f[j] = *reinterpret_cast<const float2 *>(fin + o0 + j * st);
-            l[j] = *reinterpret_cast<const float2 *>(lam + o0 + j * st);
-        }
-        if constexpr (BC) {
-            const float *sb = sbc + (neg ? N - 1 : 0);
-            const int ss = neg ? -1 : 1;
+        for (int j = 0; j < N; ++j) cp_async8(sl + j * 128, lam + o0 + j * st);
+        float2 f[N];
 #pragma unroll
-            for (int j = 0; j < N; ++j) {
+        for (int j = 0; j < N; ++j) f[j] = *reinterpret_cast<const float2 *>(fin + o0 + j * st);
+        cp_async_wait_all();
+        const float *sb = sbc + (neg ? N - 1 : 0);
+        const int ss = neg ? -1 : 1;
+        auto lget = [&](int j) {
+            float2 v = sl[j * 128];
+            if constexpr (BC) {
                 const float b = sb[j * ss];
-                l[j].x += b;
-                l[j].y += b;
+                v.x += b;
+                v.y += b;
             }
-        }
+            return v;
+        };
+        auto lput = [&](int j, float2 v) { *reinterpret_cast<float2 *>(lam + o0 + j * st) = v; };
         int ax, ay;
         float lfx, lfy;
         if (same) {
             const float2 finf = line_max(f);
+            const int2 a2 = first_max2<N>(f, finf);
             const AdjW<float2> w = adj_weights(ca, cb, finf);
             float2 lF, db;
-            adjoint_line<float2, N, PERIODIC, DB>(f, l, w, lF, db);
-            const int2 a2 = first_max2<N>(f, finf);
+            adjoint_line_acc<float2, N, PERIODIC, DB>([&](int j) { return f[j]; }, lget, lput, w,
+                                                      lF, db);
             ax = a2.x;
             ay = a2.y;
             lfx = 2.f * lF.x;
@@ -428,7 +446,7 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(const float *__restrict__
         } else if constexpr (MIXED) {
             float2 fm[N], lm[N];
 #pragma unroll
-            for (int j = 0; j < N; ++j) { fm[j] = f[j]; lm[j] = l[j]; }
+            for (int j = 0; j < N; ++j) { fm[j] = f[j]; lm[j] = lget(j); }
             int am[2];
             float lfm[2];
             const float d = adjoint_pair_mixed<N, PERIODIC, DB>(fm, lm, ca, cb, am, lfm);
@@ -436,10 +454,8 @@ __global__ void __launch_bounds__(128) k_adjoint_pairs(const float *__restrict__
             ax = am[0]; ay = am[1];
             lfx = lfm[0]; lfy = lfm[1];
 #pragma unroll
-            for (int j = 0; j < N; ++j) l[j] = lm[j];
+            for (int j = 0; j < N; ++j) lput(j, lm[j]);
         }
-#pragma unroll
-        for (int j = 0; j < N; ++j) *reinterpret_cast<float2 *>(lam + o0 + j * st) = l[j];
         lam[o0 + ax * st] += lfx;
         lam[o0 + ay * st + 1] += lfy;
     }
@@ -784,17 +800,18 @@ cudaError_t pairs_n(vp_ctx *c, const float *fin, float *lam, const LineCoef<floa
 {
     const bool db = g.axis >= 3 && lam_g;
     int *sk = c->adj_flag;
+    constexpr size_t smem = (size_t)N * 128 * sizeof(float2);     // cotangent slots
     if (db)
-        k_adjoint_pairs<N, PERIODIC, true, false, false><<<grid, 128, 0, c->stream>>>(
+        k_adjoint_pairs<N, PERIODIC, true, false, false><<<grid, 128, smem, c->stream>>>(
             fin, lam, coef, g, bc, lam_g, scale, sk);
     else if (bc)
-        k_adjoint_pairs<N, PERIODIC, false, true, false><<<grid, 128, 0, c->stream>>>(
+        k_adjoint_pairs<N, PERIODIC, false, true, false><<<grid, 128, smem, c->stream>>>(
             fin, lam, coef, g, bc, lam_g, scale, sk);
     else if (g.axis == 2 && g.mixed)
-        k_adjoint_pairs<N, PERIODIC, false, false, true><<<grid, 128, 0, c->stream>>>(
+        k_adjoint_pairs<N, PERIODIC, false, false, true><<<grid, 128, smem, c->stream>>>(
             fin, lam, coef, g, bc, lam_g, scale, sk);
     else
-        k_adjoint_pairs<N, PERIODIC, false, false, false><<<grid, 128, 0, c->stream>>>(
+        k_adjoint_pairs<N, PERIODIC, false, false, false><<<grid, 128, smem, c->stream>>>(
             fin, lam, coef, g, bc, lam_g, scale, sk);
     return cudaGetLastError();
 }
