@@ -88,9 +88,10 @@ class _Trajectory(torch.autograd.Function):
                     f.copy_(fc)
                     sim.set_accel(gc)
                     states = []
-                    for _ in range(n0, n1):
+                    for n in range(n0, n1):
                         states.append((f.clone(), sim.field()[2]))
-                        sim.step(1)
+                        if n + 1 < n1:          # f^{n1} is not needed
+                            sim.step(1)
                     for fs, gs in reversed(states):
                         sim.adjoint_step(fs, gs, lam_f, lam_g)
                     del states

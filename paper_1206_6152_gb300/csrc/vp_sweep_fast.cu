@@ -550,15 +550,20 @@ __device__ __forceinline__ long long unit_to_v(long long L, const DriftGeom &g, 
     return L * W;
 }
 
+// RHO: the per-thread compensated density sums of the N cells of the line
+// live in shared memory (slot j of thread t at j * 128 + t: conflict-free),
+// which keeps the kernel at 128 registers (16 warps per SM)
 template <typename T, int N, bool PERIODIC, bool RHO>
-__global__ void __launch_bounds__(128) k_drift_fast(const T *__restrict__ f,
-                                                   const LineCoef<T> *__restrict__ coef,
-                                                   DriftGeom g, double *__restrict__ rho_part,
-                                                   double *lost_out, T *__restrict__ fo)
+__global__ void __launch_bounds__(128, N <= 32 ? 4 : 1) k_drift_fast(const T *__restrict__ f,
+                                                               const LineCoef<T> *__restrict__ coef,
+                                                               DriftGeom g, double *__restrict__ rho_part,
+                                                               double *lost_out, T *__restrict__ fo)
 {
     typedef typename DriftVec<T>::V V;
     constexpr int W = DriftVec<T>::W;
     __shared__ Acc<double> red[32];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Acc<T> *sacc = reinterpret_cast<Acc<T> *>(smem_raw) + threadIdx.x;   // slot j: sacc[j * 128]
     const int o = blockIdx.y;
     const long long base_cell = (long long)(o / g.od) * g.m1 + (long long)(o % g.od) * g.m2;
     const long long gstride = g.cell_stride * g.nvc;
@@ -567,15 +572,23 @@ __global__ void __launch_bounds__(128) k_drift_fast(const T *__restrict__ f,
     const long long u0 = (long long)blockIdx.x * g.per_part;
     long long u1 = u0 + g.per_part;
     if (u1 > g.nunits) u1 = g.nunits;
-    Acc<T> acc[RHO ? N : 1];
+    if constexpr (RHO) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) sacc[j * 128] = Acc<T>();
+    }
     T lost = T(0);
     for (long long L = u0 + threadIdx.x; L < u1; L += blockDim.x) {
         const long long v = unit_to_v(L, g, W);
         V x[N];
+        // the line's addresses are stepped through an opaque register: the
+        // compiler would otherwise keep all 2 N of them live across the update
         const T *p = fb + v;
-        T *q = ob + v;
 #pragma unroll
-        for (int j = 0; j < N; ++j) x[j] = *reinterpret_cast<const V *>(p + j * gstride);
+        for (int j = 0; j < N; ++j) {
+            x[j] = *reinterpret_cast<const V *>(p);
+            p += gstride;
+            asm volatile("" : "+l"(p));
+        }
         if constexpr (W == 2) {
             const int via = (int)((v / g.va_stride) % g.va_n);
             const int vib = (int)(((v + 1) / g.va_stride) % g.va_n);
@@ -604,13 +617,20 @@ __global__ void __launch_bounds__(128) k_drift_fast(const T *__restrict__ f,
             const LineW<V> w = weights_one<T>(ca, line_max(x));
             lost += update_line<V, N, PERIODIC>(x, w, ca.code & 1);
         }
+        T *q = ob + v;
 #pragma unroll
-        for (int j = 0; j < N; ++j) *reinterpret_cast<V *>(q + j * gstride) = x[j];
+        for (int j = 0; j < N; ++j) {
+            *reinterpret_cast<V *>(q) = x[j];
+            q += gstride;
+            asm volatile("" : "+l"(q));
+        }
         if constexpr (RHO) {
 #pragma unroll
             for (int j = 0; j < N; ++j) {
-                if constexpr (W == 2) { acc[j].add(x[j].x); acc[j].add(x[j].y); }
-                else acc[j].add(x[j]);
+                Acc<T> a = sacc[j * 128];
+                if constexpr (W == 2) { a.add(x[j].x); a.add(x[j].y); }
+                else a.add(x[j]);
+                sacc[j * 128] = a;
             }
         }
     }
@@ -618,7 +638,7 @@ __global__ void __launch_bounds__(128) k_drift_fast(const T *__restrict__ f,
         // per-x reduction over the CTA, written as one partial per (part, cell)
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-            Acc<T> a = block_merge(acc[j], reinterpret_cast<Acc<T> *>(red));
+            Acc<T> a = block_merge(sacc[j * 128], reinterpret_cast<Acc<T> *>(red));
             if (threadIdx.x == 0)
                 rho_part[(long long)blockIdx.x * g.np + base_cell + j * g.cell_stride] = a.value();
             __syncthreads();
@@ -814,17 +834,18 @@ cudaError_t drift_fast_n(vp_ctx *c, T *f, int axis, const LineCoef<T> *coef, dou
     const bool rho = rho_part != nullptr;
     constexpr bool RHO_OK = (sizeof(T) == 4 && N <= 32) || N <= 16;
     if (rho && !RHO_OK) return cudaErrorNotSupported;
+    constexpr size_t racc = (size_t)N * 128 * sizeof(Acc<T>);   // density sums (RHO)
     if (c->periodic_space) {
         if constexpr (RHO_OK)
             if (rho) {
-                k_drift_fast<T, N, true, true><<<grid, 128, 0, c->stream>>>(f, coef, g, rho_part, &c->sc->lost, fo ? fo : f);
+                k_drift_fast<T, N, true, true><<<grid, 128, racc, c->stream>>>(f, coef, g, rho_part, &c->sc->lost, fo ? fo : f);
                 return cudaGetLastError();
             }
         k_drift_fast<T, N, true, false><<<grid, 128, 0, c->stream>>>(f, coef, g, rho_part, &c->sc->lost, fo ? fo : f);
     } else {
         if constexpr (RHO_OK)
             if (rho) {
-                k_drift_fast<T, N, false, true><<<grid, 128, 0, c->stream>>>(f, coef, g, rho_part, &c->sc->lost, fo ? fo : f);
+                k_drift_fast<T, N, false, true><<<grid, 128, racc, c->stream>>>(f, coef, g, rho_part, &c->sc->lost, fo ? fo : f);
                 return cudaGetLastError();
             }
         k_drift_fast<T, N, false, false><<<grid, 128, 0, c->stream>>>(f, coef, g, rho_part, &c->sc->lost, fo ? fo : f);
