@@ -916,7 +916,7 @@ int vp_adjoint_step(vp_ctx *c, const void *f_start, const double *g_start, void 
     // replay then keeps S5 only
     const bool yz = amax < 1.0 && vp_drift_yz_ok(c);
     if (yz) {
-        VP_CUDA_TRY(launch_drift_yz(c, S[3], c->coef_drift, S[5], nullptr));
+        VP_CUDA_TRY(launch_drift_yz(c, S[3], c->coef_drift, S[5]));
     } else {
         VP_CUDA_TRY(launch_sweep_into(c, S[3], S[4], 2, c->coef_drift, amax));
         VP_CUDA_TRY(launch_sweep_into(c, S[4], S[5], 1, c->coef_drift, amax));

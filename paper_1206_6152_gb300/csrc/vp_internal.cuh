@@ -137,11 +137,9 @@ int vp_rho_parts(vp_ctx *c);
 int vp_kick_big_ok(const vp_ctx *c);
 cudaError_t launch_kick_big(vp_ctx *c, void *f, const void *ca, const void *cb, int nsweeps,
                             int first_axis, void *fo = nullptr);
-// fused z then y drift of the whole grid (in place when fo == f); fz, if not
-// null, also receives the z sweep's output (fz != f)
+// fused z then y drift of the whole grid (in place when fo == f)
 int vp_drift_yz_ok(const vp_ctx *c);
-cudaError_t launch_drift_yz(vp_ctx *c, const void *f, const void *coef, void *fo,
-                            void *fz = nullptr);
+cudaError_t launch_drift_yz(vp_ctx *c, const void *f, const void *coef, void *fo);
 // fo: output array (nullptr: in place);
 // inter0/inter1: optional copies of the cube after sweeps 0 and 1.  gate:
 // if not null, nothing runs unless *gate != 0, and only cubes whose table

@@ -670,13 +670,12 @@ struct DriftYZ {
 };
 
 template <int N, bool PERIODIC>
-__global__ void __launch_bounds__(DriftYZ<N>::NT) k_drift_yz(const float *__restrict__ f,
-                                                           const LineCoef<float> *__restrict__ cz,
-                                                           const LineCoef<float> *__restrict__ cy,
-                                                           long long nvc, int nvy, int nvz,
-                                                           double *lost_out,
-                                                           float *__restrict__ fo,
-                                                           float *__restrict__ fz)
+__global__ void __launch_bounds__(DriftYZ<N>::NT, 2) k_drift_yz(const float *__restrict__ f,
+                                                              const LineCoef<float> *__restrict__ cz,
+                                                              const LineCoef<float> *__restrict__ cy,
+                                                              long long nvc, int nvy, int nvz,
+                                                              double *lost_out,
+                                                              float *__restrict__ fo)
 {
     constexpr int VC = DriftYZ<N>::VC, YP = DriftYZ<N>::YP, H = VC / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -688,18 +687,29 @@ __global__ void __launch_bounds__(DriftYZ<N>::NT) k_drift_yz(const float *__rest
     const long long v = v0 + 2 * vp;
     float lost = 0.f;
     float2 x[N];
+    // the CTA's block [y][z][VC] into the tile with asynchronous 16-byte
+    // copies (no register staging, few load instructions)
     {
-        const float *p = f + (x0 + (long long)r * N) * nvc + v;
+        constexpr int Q = VC / 4, PIECES = N * N * Q;
+        const float *src = f + x0 * nvc + v0;
+#pragma unroll 4
+        for (int e = t; e < PIECES; e += DriftYZ<N>::NT) {
+            const int q = e % Q, yz = e / Q, y = yz / N, z = yz % N;
+            const unsigned sa = (unsigned)__cvta_generic_to_shared(tile + y * YP + z * VC + 4 * q);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa),
+                         "l"(src + (long long)yz * nvc + 4 * q)
+                         : "memory");
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    }
+    __syncthreads();
+    {
+        // z sweep of the line (y = r, v pair), in place in the tile
+        float *q = tile + r * YP + 2 * vp;
 #pragma unroll
-        for (int j = 0; j < N; ++j) x[j] = *reinterpret_cast<const float2 *>(p + j * nvc);
+        for (int j = 0; j < N; ++j) x[j] = *reinterpret_cast<const float2 *>(q + j * VC);
         const LineCoef<float> ca = cz[(int)(v % nvz)], cb = cz[(int)((v + 1) % nvz)];
         lost += drift_pair<N, PERIODIC>(x, ca, cb);
-        if (fz) {                       // the z sweep's output as well (adjoint replay)
-            float *pz = fz + (x0 + (long long)r * N) * nvc + v;
-#pragma unroll
-            for (int j = 0; j < N; ++j) *reinterpret_cast<float2 *>(pz + j * nvc) = x[j];
-        }
-        float *q = tile + r * YP + 2 * vp;
 #pragma unroll
         for (int j = 0; j < N; ++j) *reinterpret_cast<float2 *>(q + j * VC) = x[j];
     }
@@ -711,8 +721,13 @@ __global__ void __launch_bounds__(DriftYZ<N>::NT) k_drift_yz(const float *__rest
         const LineCoef<float> c = cy[(int)((v0 / nvz) % nvy)];
         lost += drift_pair<N, PERIODIC>(x, c, c);
         float *p = fo + (x0 + r) * nvc + v;
+        const long long ys = (long long)N * nvc;
 #pragma unroll
-        for (int j = 0; j < N; ++j) *reinterpret_cast<float2 *>(p + (long long)j * N * nvc) = x[j];
+        for (int j = 0; j < N; ++j) {
+            *reinterpret_cast<float2 *>(p) = x[j];
+            p += ys;
+            asm volatile("" : "+l"(p));
+        }
     }
     if (!PERIODIC) {
         Acc<double> a;
@@ -723,7 +738,7 @@ __global__ void __launch_bounds__(DriftYZ<N>::NT) k_drift_yz(const float *__rest
 }
 
 template <int N>
-cudaError_t drift_yz_n(vp_ctx *c, const float *f, const LineCoef<float> *coef, float *fo, float *fz)
+cudaError_t drift_yz_n(vp_ctx *c, const float *f, const LineCoef<float> *coef, float *fo)
 {
     constexpr int NT = DriftYZ<N>::NT;
     const size_t smem = (size_t)N * DriftYZ<N>::YP * sizeof(float);
@@ -734,13 +749,13 @@ cudaError_t drift_yz_n(vp_ctx *c, const float *f, const LineCoef<float> *coef, f
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k_drift_yz<N, true><<<grid, NT, smem, c->stream>>>(f, cz, cy, c->nvc, c->nv[1], c->nv[2],
-                                                           &c->sc->lost, fo, fz);
+                                                           &c->sc->lost, fo);
     } else {
         cudaError_t e = cudaFuncSetAttribute(k_drift_yz<N, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k_drift_yz<N, false><<<grid, NT, smem, c->stream>>>(f, cz, cy, c->nvc, c->nv[1], c->nv[2],
-                                                            &c->sc->lost, fo, fz);
+                                                            &c->sc->lost, fo);
     }
     return cudaGetLastError();
 }
@@ -930,13 +945,11 @@ int vp_drift_yz_ok(const vp_ctx *c)
     return c->nv[2] % vc == 0 && c->n[0] <= 65535 && c->nvc / vc <= 0x7fffffffLL;
 }
 
-cudaError_t launch_drift_yz(vp_ctx *c, const void *f, const void *coef, void *fo, void *fz)
+cudaError_t launch_drift_yz(vp_ctx *c, const void *f, const void *coef, void *fo)
 {
     if (c->n[1] == 32)
-        return drift_yz_n<32>(c, (const float *)f, (const LineCoef<float> *)coef, (float *)fo,
-                              (float *)fz);
-    return drift_yz_n<16>(c, (const float *)f, (const LineCoef<float> *)coef, (float *)fo,
-                          (float *)fz);
+        return drift_yz_n<32>(c, (const float *)f, (const LineCoef<float> *)coef, (float *)fo);
+    return drift_yz_n<16>(c, (const float *)f, (const LineCoef<float> *)coef, (float *)fo);
 }
 
 // FP32 cubes of edge 48 (too large for shared memory): sweeps one pass per
