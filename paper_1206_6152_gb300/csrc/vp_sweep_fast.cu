@@ -442,66 +442,86 @@ __global__ void __launch_bounds__(128) k_kick_vx_big(const float *__restrict__ f
 
 template <int N>
 struct PlaneBig {
-    static constexpr int P = N + 1, PPC = 4, NT = PPC * N;   // planes per CTA, threads
-    static constexpr size_t SMEM = (size_t)PPC * N * P * sizeof(float);
+    static constexpr int P = N + 1, PPC = 4, NT = PPC * N;   // planes per group, threads
+    static constexpr int G = N / PPC;                         // groups per cube
+    static constexpr int TILE = PPC * N * P;                  // floats per buffer
+    static constexpr size_t SMEM = (size_t)2 * TILE * sizeof(float);
 };
 
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// Persistent: each CTA takes groups of PPC consecutive vx planes in turn
+// (group g: cube g / G, planes (g % G) PPC ...) with two tile buffers; the
+// next group is copied asynchronously (cp.async, 4 bytes a thread per
+// element: the odd pitch keeps rows and columns conflict-free) while the
+// current one is swept.  Groups are disjoint, so in-place use (fo == f) is
+// safe.
 template <int N>
 __global__ void __launch_bounds__(PlaneBig<N>::NT, 3) k_kick_plane_big(
     const float *__restrict__ f, const LineCoef<float> *__restrict__ c0, int a0,
-    const LineCoef<float> *__restrict__ c1, int a1, int nsw, double *lost_out,
+    const LineCoef<float> *__restrict__ c1, int a1, int nsw, long long ngroups, double *lost_out,
     float *__restrict__ fo)
 {
     constexpr int P = PlaneBig<N>::P, PPC = PlaneBig<N>::PPC, NT = PlaneBig<N>::NT;
+    constexpr int G = PlaneBig<N>::G, TILE = PlaneBig<N>::TILE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *tile = reinterpret_cast<float *>(smem_raw);
+    float *tiles = reinterpret_cast<float *>(smem_raw);
     __shared__ Acc<double> red[32];
     const int t = threadIdx.x, pl = t / N, m = t % N;
-    const long long cell = blockIdx.x;
-    const int i0 = blockIdx.y * PPC;                      // first plane of the CTA
-    const float *g = f + (cell * N + i0) * (long long)N * N;   // PPC contiguous planes
-    float *go = fo + (cell * N + i0) * (long long)N * N;
     // thread t moves column t % N of rows t / N, t / N + NT / N, ... (the
-    // PPC planes are PPC * N contiguous rows)
+    // PPC planes of a group are PPC * N contiguous rows)
     constexpr int RS = NT / N, NR = PPC * N / RS;         // rows per step, rows per thread
-    {
-        float v[NR];                                      // all loads in flight at once
-        const float *gp = g + (t / N) * N + m;
-#pragma unroll
-        for (int i = 0; i < NR; ++i) v[i] = gp[i * RS * N];
-        float *tp = tile + (t / N) * P + m;
-#pragma unroll
-        for (int i = 0; i < NR; ++i) tp[i * RS * P] = v[i];
-    }
-    __syncthreads();
+    auto issue = [&](long long g, float *buf) {
+        const float *src = f + ((g / G) * N + (g % G) * PPC) * (long long)N * N + (t / N) * N + m;
+        float *dst = buf + (t / N) * P + m;
+#pragma unroll 8
+        for (int i = 0; i < NR; ++i) cp_async4(dst + i * RS * P, src + i * RS * N);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
     float lost = 0.f;
-    float *pt = tile + pl * N * P;
-    for (int sw = 0; sw < nsw; ++sw) {
-        const int va = sw ? a1 : a0;
-        const LineCoef<float> cf = (sw ? c1 : c0)[cell * 3 + va];
-        float *L = va == 1 ? pt + m : pt + m * P;          // column m (vy) or row m (vz)
-        const int st = va == 1 ? P : 1;
-        if ((cf.code >> 1) == 0) {
-            float x[N];
-#pragma unroll
-            for (int j = 0; j < N; ++j) x[j] = L[j * st];
-            const LineW<float> w = weights_one<float>(cf, line_max(x));
-            lost += update_line<float, N, false>(x, w, cf.code & 1);
-#pragma unroll
-            for (int j = 0; j < N; ++j) L[j * st] = x[j];
+    long long g = blockIdx.x;
+    if (g < ngroups) issue(g, tiles);
+    for (int b = 0; g < ngroups; g += gridDim.x, b ^= 1) {
+        float *cur = tiles + b * TILE, *nxt = tiles + (b ^ 1) * TILE;
+        const long long gn = g + gridDim.x;
+        if (gn < ngroups) {
+            issue(gn, nxt);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
         } else {
-            lost += kick_line_shifted(L, st, N, cf);
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         __syncthreads();
-    }
-    {
-        float v[NR];
-        const float *tp = tile + (t / N) * P + m;
+        const long long cell = g / G;
+        float *pt = cur + pl * N * P;
+        for (int sw = 0; sw < nsw; ++sw) {
+            const int va = sw ? a1 : a0;
+            const LineCoef<float> cf = (sw ? c1 : c0)[cell * 3 + va];
+            float *L = va == 1 ? pt + m : pt + m * P;      // column m (vy) or row m (vz)
+            const int st = va == 1 ? P : 1;
+            if ((cf.code >> 1) == 0) {
+                float x[N];
 #pragma unroll
-        for (int i = 0; i < NR; ++i) v[i] = tp[i * RS * P];
-        float *gp = go + (t / N) * N + m;
+                for (int j = 0; j < N; ++j) x[j] = L[j * st];
+                const LineW<float> w = weights_one<float>(cf, line_max(x));
+                lost += update_line<float, N, false>(x, w, cf.code & 1);
 #pragma unroll
-        for (int i = 0; i < NR; ++i) gp[i * RS * N] = v[i];
+                for (int j = 0; j < N; ++j) L[j * st] = x[j];
+            } else {
+                lost += kick_line_shifted(L, st, N, cf);
+            }
+            __syncthreads();
+        }
+        {
+            const float *tp = cur + (t / N) * P + m;
+            float *gp = fo + (cell * N + (g % G) * PPC) * (long long)N * N + (t / N) * N + m;
+#pragma unroll 8
+            for (int i = 0; i < NR; ++i) gp[i * RS * N] = tp[i * RS * P];
+        }
+        __syncthreads();        // the buffer is refilled two groups later
     }
     Acc<double> a;
     a.add((double)lost);
@@ -985,10 +1005,15 @@ cudaError_t launch_kick_big(vp_ctx *c, void *f_, const void *ca_, const void *cb
         if ((e = cudaFuncSetAttribute(k_kick_plane_big<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)PB::SMEM)) != cudaSuccess)
             return e;
-        const dim3 grid((unsigned)c->np, (unsigned)(N / PB::PPC));
-        k_kick_plane_big<N><<<grid, PB::NT, PB::SMEM, c->stream>>>(sw ? fo : f, cf, va,
-                                                                   sw + 1 < 3 ? ca : cb, vb, nsw,
-                                                                   &c->sc->lost, fo);
+        int per_sm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_kick_plane_big<N>, PB::NT,
+                                                               PB::SMEM)) != cudaSuccess)
+            return e;
+        const long long ngroups = c->np * PB::G;
+        long long grid = (long long)vp_sm_count() * (per_sm > 0 ? per_sm : 1);
+        if (grid > ngroups) grid = ngroups;
+        k_kick_plane_big<N><<<(unsigned)grid, PB::NT, PB::SMEM, c->stream>>>(
+            sw ? fo : f, cf, va, sw + 1 < 3 ? ca : cb, vb, nsw, ngroups, &c->sc->lost, fo);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         sw += nsw;
     }
