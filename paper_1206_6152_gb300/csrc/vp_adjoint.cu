@@ -854,7 +854,7 @@ int adjoint_step_two_states(vp_ctx *c, const void *S0, void *lambda_f, double *l
     VP_CUDA_TRY(launch_drift_adjoint(c, X, lambda_f, 0, c->coef_drift, c->rho2));
     // replay to S3 (and S4, unless the fused y+z adjoint recomputes it)
     TRY(replay_k1(c, S0, X, k1));                                                 // X = S3
-    if (amax < 1.0 && vp_drift_yz_ok(c)) {
+    if (amax < 1.0 && vp_drift_adjoint_yz_ok(c)) {
         VP_CUDA_TRY(launch_drift_adjoint_yz(c, X, lambda_f, c->coef_drift));
     } else {
         VP_CUDA_TRY(launch_sweep_into(c, X, Y, 2, c->coef_drift, amax));          // Y = S4
@@ -914,7 +914,7 @@ int vp_adjoint_step(vp_ctx *c, const void *f_start, const double *g_start, void 
     }
     // the fused y+z drift adjoint recomputes the y input S4 from S3: the
     // replay then keeps S5 only
-    const bool yz = amax < 1.0 && vp_drift_yz_ok(c);
+    const bool yz = amax < 1.0 && vp_drift_adjoint_yz_ok(c);
     if (yz) {
         VP_CUDA_TRY(launch_drift_yz(c, S[3], c->coef_drift, S[5]));
     } else {

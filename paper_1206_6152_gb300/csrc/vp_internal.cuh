@@ -137,7 +137,8 @@ int vp_rho_parts(vp_ctx *c);
 int vp_kick_big_ok(const vp_ctx *c);
 cudaError_t launch_kick_big(vp_ctx *c, void *f, const void *ca, const void *cb, int nsweeps,
                             int first_axis, void *fo = nullptr);
-// fused z then y drift of the whole grid (in place when fo == f)
+// fused z then y drift of the whole grid (FP32, N_y = N_z in {16, 32}; in
+// place when fo == f)
 int vp_drift_yz_ok(const vp_ctx *c);
 cudaError_t launch_drift_yz(vp_ctx *c, const void *f, const void *coef, void *fo);
 // fo: output array (nullptr: in place);
@@ -179,7 +180,7 @@ int vp_adjoint_pairs_ok(const vp_ctx *c, int axis);
 int vp_kick_adjoint3_ok(const vp_ctx *c);
 // the y then z drift adjoints of a zero-shift step in one pass (FP32,
 // N_y = N_z in {16, 32}); s3: the input of the z drift (the input of the y
-// drift is recomputed from it); the same grids as launch_drift_yz
+// drift is recomputed from it); the grids of launch_drift_yz for those N
 int vp_drift_adjoint_yz_ok(const vp_ctx *c);
 cudaError_t launch_drift_adjoint_yz(vp_ctx *c, const void *s3, void *lam, const void *coef);
 cudaError_t launch_kick_adjoint3(vp_ctx *c, const void *sa, const void *sb, void *lam,

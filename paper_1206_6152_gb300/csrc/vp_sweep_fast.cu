@@ -686,7 +686,9 @@ template <int N>
 struct DriftYZ {
     static constexpr int VC = 512 / N;                 // velocity cells per CTA
     static constexpr int NT = N * VC / 2;              // threads: one line pair each
-    static constexpr int YP = N * VC + (VC == 16 ? 16 : 0);   // tile pitch of one y
+    // tile pitch of one y: the r groups of a warp's z-sweep accesses (VC/2
+    // lanes each) start on different banks
+    static constexpr int YP = N * VC + (VC == 16 ? 16 : 0);
 };
 
 template <int N, bool PERIODIC>
@@ -867,9 +869,18 @@ cudaError_t drift_fast_n(vp_ctx *c, T *f, int axis, const LineCoef<T> *coef, dou
     g.per_part = (g.nunits + nparts - 1) / nparts;
     dim3 grid((unsigned)nparts, (unsigned)outer);
     const bool rho = rho_part != nullptr;
-    constexpr bool RHO_OK = (sizeof(T) == 4 && N <= 32) || N <= 16;
+    constexpr bool RHO_OK = (sizeof(T) == 4 && N <= 48) || N <= 16;
     if (rho && !RHO_OK) return cudaErrorNotSupported;
     constexpr size_t racc = (size_t)N * 128 * sizeof(Acc<T>);   // density sums (RHO)
+    if constexpr (RHO_OK) {
+        if (rho) {
+            cudaError_t e = cudaFuncSetAttribute(c->periodic_space ? k_drift_fast<T, N, true, true>
+                                                                   : k_drift_fast<T, N, false, true>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)racc);
+            if (e != cudaSuccess) return e;
+        }
+    }
     if (c->periodic_space) {
         if constexpr (RHO_OK)
             if (rho) {
@@ -921,7 +932,7 @@ int vp_drift_fast_ok(const vp_ctx *c, int axis)
 
 int vp_rho_fuse_ok(const vp_ctx *c)
 {
-    return vp_drift_fast_ok(c, 0) && c->n[0] <= (c->isdouble ? 16 : 32);
+    return vp_drift_fast_ok(c, 0) && c->n[0] <= (c->isdouble ? 16 : 48);
 }
 
 cudaError_t launch_kick_fast(vp_ctx *c, void *f, const void *ca, const void *cb, int nsweeps,
@@ -949,7 +960,7 @@ cudaError_t launch_drift_fast(vp_ctx *c, void *f, int axis, const void *coef, do
     switch (n) {
     case 16: return drift_fast_n<float, 16>(c, (float *)f, axis, cf, rho_part, np, o);
     case 32: return drift_fast_n<float, 32>(c, (float *)f, axis, cf, rho_part, np, o);
-    case 48: return drift_fast_n<float, 48>(c, (float *)f, axis, cf, nullptr, 0, o);
+    case 48: return drift_fast_n<float, 48>(c, (float *)f, axis, cf, rho_part, np, o);
     default: return drift_fast_n<float, 64>(c, (float *)f, axis, cf, nullptr, 0, o);
     }
 }
@@ -960,6 +971,8 @@ int vp_drift_yz_ok(const vp_ctx *c)
 {
     if (c->isdouble || c->n[1] != c->n[2]) return 0;
     const int n = c->n[1];
+    // (lines of 48: two register-line passes, each near the HBM bound, beat
+    // a fused pass of 8-cell chunks)
     if (n != 16 && n != 32) return 0;
     const int vc = 512 / n;
     return c->nv[2] % vc == 0 && c->n[0] <= 65535 && c->nvc / vc <= 0x7fffffffLL;

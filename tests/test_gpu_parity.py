@@ -215,6 +215,28 @@ def test_fused_yz_drift_steps(shape, space_bc):
 
 
 @pytest.mark.gpu
+def test_split_steps_48_lines():
+    """FP32 lines of 48 along x, y and z: the x drift with the fused density
+    (the density sums in shared memory) and the register-line z and y drifts
+    (the vz bounds put one pair of z lines across v_z = 0)."""
+    w = I.small_maxwell(n=(48, 48, 48), nv=(2, 2, 8), dtype="f32", amp=0.3, G=25.0)
+    w = w.replace(box_lo=(-0.5,) * 3, box_hi=(0.5,) * 3, vlo=(-4.0, -4.0, -4.0),
+                  vhi=(4.0, 4.0, 6.0))
+    f0 = I.initial_condition(w)
+    sim, f = gpu_sim(w, f0)
+    t = sim.step(3, sync=True)
+    got = f.cpu().numpy().astype(np.float64)
+    rho_g = sim.field()[0].cpu().numpy()
+    ref = O.Simulation(f0.astype(np.float64), O.Grid.of(w), O.Params.of(w))
+    ref.step(3)
+    assert abs(t - ref.t) <= 1e-6 * ref.t
+    assert rel_l1(got, ref.f) <= 1e-5
+    assert got.min() >= 0.0
+    assert np.abs(rho_g - ref.rho).max() <= 2e-6 * ref.rho.max()
+    sim.close()
+
+
+@pytest.mark.gpu
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_landau_16_20_steps(dtype):
     """The 16^3 x 16^3 Landau-damping workload, 20 steps: relative L1(f) vs
