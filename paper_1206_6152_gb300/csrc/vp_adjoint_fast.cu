@@ -16,24 +16,33 @@
 //   dl_j     += (c0 + 2 c1 - 2 c2) mu - 3 a I1 + 3 b I2,
 //   dl_{j+1} += a I1,     dl_{j-1} -= b I2,
 //   l_F      += a (u1 I1 - s1) + b (s2 - u2 I2)    (dE+/dF, dE-/dF),
+// where u I - s is minus the indicator of the arm saturated at 1 (so l_F is
+// accumulated per line as c2 sum mu g2 - c1 sum mu g1, g = s - I u),
 // and l_F reaches the line maximum (2 l_F on f_inf) at its first position
 // in upwind order.  The velocity sweeps also return
 //   d/dbeta = sum_j mu_j (f_j + c1'(beta) E+ + c2'(beta) E-).
 // The limiter values are the forward kernels' own (same F, h, r3 and
 // saturating FMAs), so the arms are those the forward pass took.
 //
+// Every kernel runs one upwind code path: a line with u < 0 is read and
+// written mirrored (from its far end with a negative stride, or through a
+// tile held in upwind order).
+//
 // Kernels:
 //  * k_adjoint_pairs: two lines per thread (adjacent vz for the vx and vy
-//    sweeps, adjacent velocity cells for the drifts), packed f32x2, state
-//    and cotangent read straight from global memory (a warp reads two
-//    128-byte rows per load).  The x-drift adjoint can add the broadcast of
-//    the density cotangent on load.
+//    sweeps, adjacent velocity cells for the drifts), packed f32x2; the
+//    state line read from global memory into registers, the cotangent line
+//    copied by cp.async into the thread's shared-memory slots and streamed
+//    from there (a warp reads two 128-byte rows per load).  The x-drift
+//    adjoint can add the broadcast of the density cotangent on load.
 //  * k_adjoint_rows: the vz sweep; each warp stages 32 rows of the state and
 //    of the cotangent in shared memory with coalesced 16-byte loads, one row
 //    per lane, and writes the rows back the same way.
 //  * k_kick_adjoint_zy: the vz and then the vy adjoint of a half kick on the
 //    same staged rows (a warp holds whole vx planes), followed by the vx
 //    adjoint as line pairs: the cotangent crosses HBM twice for three sweeps.
+//  * k_drift_adjoint_yz: the y and then the z drift adjoint in one pass,
+//    the y input recomputed from the z input in a shared tile.
 #include <cuda_runtime.h>
 
 #include "vp_device.cuh"

@@ -14,7 +14,11 @@
 //    (a warp reads 256 contiguous bytes per load), updates them and stores
 //    them back.  Optionally (x sweep) it accumulates the density of the
 //    updated f: per-thread double-float sums over the velocity cells it
-//    visits, one reduction per CTA into a small partial buffer.
+//    visits (kept in the thread's shared-memory slots), one reduction per
+//    CTA into a small partial buffer.
+//  * k_drift_yz<N>: the z and the y drift in one pass through a shared tile.
+//  * k_kick6<N>: the six sweeps of two consecutive half kicks in one pass.
+//  * k_kick_vx_big / k_kick_plane_big: cubes of 48^3, above shared memory.
 #include <cuda_runtime.h>
 
 #include "vp_device.cuh"
@@ -674,12 +678,13 @@ __global__ void __launch_bounds__(128, N <= 32 ? 4 : 1) k_drift_fast(const T *__
 
 // ---------------------------------------------------------------------------
 // fused z and y drift (FP32, N_y = N_z = N): one CTA per (x, chunk of VC
-// velocity cells).  The z sweep reads its lines (pairs of adjacent velocity
-// cells) straight from global memory and writes them to a shared tile
-// [y][z][VC]; the y sweep reads its lines from the tile and writes them
-// straight back.  f crosses HBM once for both sweeps.  The chunk lies inside
-// one vz row, so every y line of the CTA has the same v_y; the z lines of a
-// pair differ in v_z (two coefficients, two scalar lines where the pair
+// velocity cells).  The CTA's block [y][z][VC] is copied into a shared tile
+// with 16-byte cp.async copies; the z sweep takes its lines (pairs of
+// adjacent velocity cells) from the tile and writes them back in place; the
+// y sweep reads its lines from the tile and writes them straight to global
+// memory.  f crosses HBM once for both sweeps.  The chunk lies inside one vz
+// row, so every y line of the CTA has the same v_y; the z lines of a pair
+// differ in v_z (two coefficients, two scalar lines where the pair
 // straddles the sign change of v_z).
 // ---------------------------------------------------------------------------
 template <int N>
