@@ -874,7 +874,7 @@ cudaError_t drift_fast_n(vp_ctx *c, T *f, int axis, const LineCoef<T> *coef, dou
     g.per_part = (g.nunits + nparts - 1) / nparts;
     dim3 grid((unsigned)nparts, (unsigned)outer);
     const bool rho = rho_part != nullptr;
-    constexpr bool RHO_OK = (sizeof(T) == 4 && N <= 48) || N <= 16;
+    constexpr bool RHO_OK = (sizeof(T) == 4 && N <= 64) || N <= 16;
     if (rho && !RHO_OK) return cudaErrorNotSupported;
     constexpr size_t racc = (size_t)N * 128 * sizeof(Acc<T>);   // density sums (RHO)
     if constexpr (RHO_OK) {
@@ -937,7 +937,7 @@ int vp_drift_fast_ok(const vp_ctx *c, int axis)
 
 int vp_rho_fuse_ok(const vp_ctx *c)
 {
-    return vp_drift_fast_ok(c, 0) && c->n[0] <= (c->isdouble ? 16 : 48);
+    return vp_drift_fast_ok(c, 0) && c->n[0] <= (c->isdouble ? 16 : 64);
 }
 
 cudaError_t launch_kick_fast(vp_ctx *c, void *f, const void *ca, const void *cb, int nsweeps,
@@ -966,7 +966,7 @@ cudaError_t launch_drift_fast(vp_ctx *c, void *f, int axis, const void *coef, do
     case 16: return drift_fast_n<float, 16>(c, (float *)f, axis, cf, rho_part, np, o);
     case 32: return drift_fast_n<float, 32>(c, (float *)f, axis, cf, rho_part, np, o);
     case 48: return drift_fast_n<float, 48>(c, (float *)f, axis, cf, rho_part, np, o);
-    default: return drift_fast_n<float, 64>(c, (float *)f, axis, cf, nullptr, 0, o);
+    default: return drift_fast_n<float, 64>(c, (float *)f, axis, cf, rho_part, np, o);
     }
 }
 

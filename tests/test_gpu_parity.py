@@ -215,11 +215,13 @@ def test_fused_yz_drift_steps(shape, space_bc):
 
 
 @pytest.mark.gpu
-def test_split_steps_48_lines():
-    """FP32 lines of 48 along x, y and z: the x drift with the fused density
-    (the density sums in shared memory) and the register-line z and y drifts
-    (the vz bounds put one pair of z lines across v_z = 0)."""
-    w = I.small_maxwell(n=(48, 48, 48), nv=(2, 2, 8), dtype="f32", amp=0.3, G=25.0)
+@pytest.mark.parametrize("n, space_bc", [((48, 48, 48), "periodic"), ((64, 8, 8), "periodic"),
+                                         ((64, 8, 8), "outflow")])
+def test_split_steps_long_lines(n, space_bc):
+    """FP32 lines of 48 (x, y and z) and 64 (x): the x drift with the fused
+    density (the density sums in shared memory) and the register-line z and
+    y drifts (the vz bounds put one pair of z lines across v_z = 0)."""
+    w = I.small_maxwell(n=n, nv=(2, 2, 8), dtype="f32", amp=0.3, G=25.0, space_bc=space_bc)
     w = w.replace(box_lo=(-0.5,) * 3, box_hi=(0.5,) * 3, vlo=(-4.0, -4.0, -4.0),
                   vhi=(4.0, 4.0, 6.0))
     f0 = I.initial_condition(w)
