@@ -155,11 +155,13 @@ int vp_stats(vp_ctx *ctx, long long *kernels_launched);
 /* Discrete adjoint of one split step (not in the paper; limiter branches,
  * integer shifts and line-maximum positions frozen at the forward pass).
  * Requires dt_fixed > 0 (VP_ERR_STATE otherwise).  On first use the
- * context allocates its scratch states plus small tables: nine states (the
- * inputs of the nine sweeps of the replayed step) or, where they do not
- * fit or vp_set_adjoint_states asks for it, two states with which the
- * inputs are recomputed from f_start in four partial replays (about 2.5
- * times the passes over f); VP_ERR_OOM if even two do not fit.
+ * context allocates its scratch states plus small tables: the inputs of the
+ * sweeps of the replayed step that its adjoint reads (at most eight states
+ * of f's size; six for FP32 velocity cubes of edge 16 or 32 with fused y+z
+ * drifts) or, where they do not fit or vp_set_adjoint_states asks for it,
+ * two states with which the inputs are recomputed from f_start in four
+ * partial replays (about 2.5 times the passes over f); VP_ERR_OOM if even
+ * two do not fit.
  *   f_start: the step-start f^n (device, same layout/dtype as f; read only)
  *   g_start: the step-start acceleration g^n (3 N^p doubles, device)
  *   lambda_f: in: cotangent of f^{n+1}; out: cotangent of f^n (device,
@@ -168,9 +170,10 @@ int vp_stats(vp_ctx *ctx, long long *kernels_launched);
  *             doubles, device)
  * The context's own f is not modified; the context's scratch is used to
  * replay the forward step. */
-/* Scratch policy of vp_adjoint_step (not in the paper): 0 automatic (nine
- * states if they fit, else two), 1 two states (recompute), 2 nine states.
- * Frees the scratch held so far; VP_ERR_ARG for another mode. */
+/* Scratch policy of vp_adjoint_step (not in the paper): 0 automatic (the
+ * kept sweep inputs if they fit, else two states), 1 two states
+ * (recompute), 2 the kept sweep inputs.  Frees the scratch held so far;
+ * VP_ERR_ARG for another mode. */
 int vp_set_adjoint_states(vp_ctx *ctx, int mode);
 
 int vp_adjoint_step(vp_ctx *ctx, const void *f_start, const double *g_start,

@@ -599,32 +599,35 @@ inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
         if (_r != VP_OK) return _r; \
     } while (0)
 
-void free_adjoint_states(vp_ctx *c)
-{
-    if (!c->adj_states) return;
-    for (int i = 0; i < c->adj_nstates; ++i)
-        if (c->adj_states[i]) cudaFree(c->adj_states[i]);
-    free(c->adj_states);
-    c->adj_states = nullptr;
-    c->adj_nstates = 0;
-}
-
-// n states of f's size; false (nothing kept) if they do not fit
-bool alloc_adjoint_states(vp_ctx *c, int n)
+// n slots of f's size, allocated where want[i] (slots marked with the same
+// alias share one buffer: alias[i] = i, or the index of the slot whose
+// buffer it uses); false (nothing kept) if they do not fit
+bool alloc_adjoint_states(vp_ctx *c, int n, const bool *want, const int *alias)
 {
     const size_t bytes = (size_t)c->ncells * c->esize;
     c->adj_states = (void **)calloc(n, sizeof(void *));
     if (!c->adj_states) return false;
     c->adj_nstates = n;
-    for (int i = 0; i < n; ++i)
+    for (int i = 0; i < n; ++i) {
+        if (!want[i]) continue;
+        if (alias[i] != i) {
+            c->adj_states[i] = c->adj_states[alias[i]];
+            continue;
+        }
         if (cudaMalloc(&c->adj_states[i], bytes) != cudaSuccess) {
             cudaGetLastError();
-            free_adjoint_states(c);
+            vp_free_adjoint_states(c);
             return false;
         }
+    }
     return true;
 }
 
+// The nine-slot mode keeps S1..S8 (S[k]: the input of sweep k of the step;
+// S0 = f^n is the caller's): only the slots the step's path reads — with
+// the register kick adjoint S2 and S8 are scratch for the fix-up of
+// shifted cubes only and share one buffer, and with the fused y+z drift
+// adjoint S4 is not kept.
 int ensure_adjoint_scratch(vp_ctx *c)
 {
     if (c->adj_states) return VP_OK;
@@ -642,15 +645,45 @@ int ensure_adjoint_scratch(vp_ctx *c)
             return VP_ERR_OOM;
         }
     }
-    if (c->adj_mode != 1 && alloc_adjoint_states(c, 9)) return VP_OK;
+    if (c->adj_mode != 1) {
+        const bool reg = vp_kick_adjoint3_ok(c);
+        const bool yz = vp_drift_alpha_bound(c, c->cfg.dt_fixed) < 1.0 && vp_drift_adjoint_yz_ok(c);
+        bool want[9];
+        int alias[9];
+        for (int i = 0; i < 9; ++i) {
+            want[i] = i > 0;
+            alias[i] = i;
+        }
+        if (reg) alias[8] = 2;
+        if (yz) want[4] = false;
+        if (alloc_adjoint_states(c, 9, want, alias)) return VP_OK;
+    }
     if (c->adj_mode == 2) return VP_ERR_OOM;
-    return alloc_adjoint_states(c, 2) ? VP_OK : VP_ERR_OOM;
+    const bool two[2] = {true, true};
+    const int id[2] = {0, 1};
+    return alloc_adjoint_states(c, 2, two, id) ? VP_OK : VP_ERR_OOM;
 }
 
 // scalar on the device used as the replay's tau
 __global__ void k_set(double *p, double v) { *p = v; }
 
 }  // namespace
+
+// frees the adjoint's scratch states (each buffer once: slots may share one)
+void vp_free_adjoint_states(vp_ctx *c)
+{
+    if (!c->adj_states) return;
+    for (int i = 0; i < c->adj_nstates; ++i) {
+        void *p = c->adj_states[i];
+        if (!p) continue;
+        bool seen = false;
+        for (int j = 0; j < i; ++j) seen |= c->adj_states[j] == p;
+        if (!seen) cudaFree(p);
+    }
+    free(c->adj_states);
+    c->adj_states = nullptr;
+    c->adj_nstates = 0;
+}
 
 cudaError_t launch_drift_adjoint(vp_ctx *c, const void *fin, void *lam, int axis, const void *coef,
                                  const double *bc)
@@ -797,7 +830,7 @@ int vp_set_adjoint_states(vp_ctx *c, int mode)
         cudaGetLastError();
         return VP_ERR_CUDA;
     }
-    free_adjoint_states(c);
+    vp_free_adjoint_states(c);
     c->adj_mode = mode;
     return VP_OK;
 }

@@ -48,11 +48,7 @@ void free_ctx(vp_ctx *c)
                     c->adj_tmp, c->adj_flag};
     for (void *b : bufs)
         if (b) cudaFree(b);
-    if (c->adj_states) {
-        for (int i = 0; i < c->adj_nstates; ++i)
-            if (c->adj_states[i]) cudaFree(c->adj_states[i]);
-        free(c->adj_states);
-    }
+    vp_free_adjoint_states(c);
     if (c->sc_host) cudaFreeHost(c->sc_host);
     if (c->cap) cudaStreamDestroy(c->cap);
     delete c;

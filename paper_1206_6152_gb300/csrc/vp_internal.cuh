@@ -94,9 +94,10 @@ struct vp_ctx {
     double *adj_lg;             // 3 np
     double *adj_tmp;            // nfft
     int *adj_flag;              // set when the register adjoint skipped a line
-    void **adj_states;          // sweep inputs (f's dtype): nine, or two to recompute into
+    void **adj_states;          // sweep inputs (f's dtype): nine slots (those the path
+                                // reads; some may share a buffer), or two to recompute into
     int adj_nstates;
-    int adj_mode;               // 0 automatic, 1 two states, 2 nine states
+    int adj_mode;               // 0 automatic, 1 two states, 2 the kept sweep inputs
 };
 
 // ---------------------------------------------------------------------------
@@ -182,6 +183,8 @@ int vp_kick_adjoint3_ok(const vp_ctx *c);
 // N_y = N_z in {16, 32}); s3: the input of the z drift (the input of the y
 // drift is recomputed from it); the grids of launch_drift_yz for those N
 int vp_drift_adjoint_yz_ok(const vp_ctx *c);
+// frees the adjoint's scratch states (each buffer once)
+void vp_free_adjoint_states(vp_ctx *c);
 cudaError_t launch_drift_adjoint_yz(vp_ctx *c, const void *s3, void *lam, const void *coef);
 cudaError_t launch_kick_adjoint3(vp_ctx *c, const void *sa, const void *sb, void *lam,
                                  const void *coef, double *lam_g, double tau);

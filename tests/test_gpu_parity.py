@@ -334,6 +334,42 @@ def test_jeans_32_full_size_two_steps():
     assert abs(e["M"] + e["M_out"] - M0) <= 1e-7 * M0
 
 
+@pytest.mark.gpu
+@pytest.mark.slow
+def test_jeans_32_growth_rate_over_200_steps():
+    """The 32^3 x 32^3 FP32 Jeans workload over its 200 steps: the density
+    mode grows at the rate of the Maxwellian dispersion relation (k/k_J =
+    0.5, gamma = y sqrt(2) k sigma); fitted where the growing root dominates
+    (the density starts with zero time derivative) and the amplitude is still
+    linear (below 1e-1).  Mass is conserved and f stays non-negative."""
+    from scipy.optimize import brentq
+    from scipy.special import erfcx
+    w = I.jeans_c2()
+    f0 = I.initial_condition(w)
+    sim, f = gpu_sim(w, f0)
+    del f0
+    M0 = sim.energy()["M"]
+    ts, amps = [], []
+    t = 0.0
+    for _ in range(w.steps):
+        rho = sim.density().cpu().numpy().reshape(w.n)
+        ts.append(t)
+        amps.append(abs(np.fft.fftn(rho / rho.mean() - 1.0)[1, 0, 0]) * 2 / rho.size)
+        t = sim.step(1, sync=True)
+    e = sim.energy()
+    assert float(f.min()) >= 0.0
+    sim.close()
+    ts, amps = np.array(ts), np.array(amps)
+    k = 2 * math.pi / (w.box_hi[0] - w.box_lo[0])
+    y = brentq(lambda y: 1 - math.sqrt(math.pi) * y * erfcx(y) - 0.25, 1e-9, 50)
+    gamma = y * math.sqrt(2) * k * w.sigma
+    sel = (ts > 0.25) & (amps < 0.1)
+    assert sel.sum() > 20
+    slope = np.polyfit(ts[sel], np.log(amps[sel]), 1)[0]
+    assert slope == pytest.approx(gamma, rel=0.05)
+    assert abs(e["M"] + e["M_out"] - M0) <= 1e-6 * M0
+
+
 def device_initial_condition(w, dtype=torch.float32):
     """initial_condition(w) built on the GPU from its two FP64 factors (the
     same products, rounded once)."""
