@@ -18,6 +18,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytestmark = pytest.mark.skip(reason="needs a CUDA GPU")
 
+from conftest import golden  # noqa: E402
 from oracle import vp_oracle as O  # noqa: E402
 from paper_1206_6152_gb300 import inputs as I  # noqa: E402
 
@@ -153,18 +154,19 @@ def test_galilean_shift_keeps_the_growth_rate(vt_over_sigma):
 # 3.454, 2.425, -0.580, -7.0 against 3.492, 2.436, -0.578, -6.64).  At
 # k/k_J = 2.0 the velocity bound V = L/T cuts the Maxwellian at 1.8 sigma,
 # hence the wider tolerance.
-PAPER_RUNS = [
-    (0.1, 0.01, (0.5, 1.0), 0.03),
-    (0.5, 0.01, (0.3, 1.0), 0.03),
-    (1.1, 0.1, (0.3, 1.0), 0.03),
-    (2.0, 0.1, (0.1, 0.4), 0.10),
-]
+T2 = golden("paper_test2")
+T3 = golden("paper_test3")
+FIT = {0.1: ((0.5, 1.0), 0.03), 0.5: ((0.3, 1.0), 0.03), 1.1: ((0.3, 1.0), 0.03),
+       2.0: ((0.1, 0.4), 0.10)}
+PAPER_RUNS = [(kk, T2["amplitude_below_kJ"] if kk < 1 else T2["amplitude_above_kJ"]) + FIT[kk]
+              for kk in T2["k_over_kJ"]]
 
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("kk, amp, window, tol", PAPER_RUNS)
 def test_test2_runs_of_the_paper(kk, amp, window, tol):
-    f0, sigma, k = maxwell_1d(128, 128, kk, amp)
+    nx, nv = int(T2["nx"]), int(T2["nv"])
+    f0, sigma, k = maxwell_1d(nx, nv, kk, amp, n_mode=int(T2["n_mode"]))
     ts, amps = run_gpu(f0, window[1] + 0.01)
     y = growth_root(kk) if kk < 1 else -damping_root(kk)
     theory = y * math.sqrt(2) * k * sigma
@@ -172,7 +174,7 @@ def test_test2_runs_of_the_paper(kk, amp, window, tol):
     slope = np.polyfit(ts[sel], np.log(amps[sel]), 1)[0]
     assert slope == pytest.approx(theory, rel=tol)
     # the same run in the oracle, first 30 steps
-    ref = O.Simulation(f0.reshape(128, 1, 1, 128, 1, 1).copy(), grid_1d(128, 128, 1.0, 1.0),
+    ref = O.Simulation(f0.reshape(nx, 1, 1, nv, 1, 1).copy(), grid_1d(nx, nv, 1.0, 1.0),
                        O.Params(G=1.0, courant=0.5))
     for n in range(30):
         assert abs(ref.t - ts[n]) <= 1e-12 * max(ts[n], 1.0)
@@ -185,7 +187,7 @@ def test_test2_energy_and_mass_conservation():
     """Sec. 3.2: E within 1e-3 and M within 1e-6 (k/k_J = 0.5, 128 x 128), up
     to t = 1.75 T (past 2 T the collapsing sheet is under-resolved on 128
     cells and the energy error grows past 1e-3, as in the oracle)."""
-    f0, sigma, k = maxwell_1d(128, 128, 0.5, 0.01)
+    f0, sigma, k = maxwell_1d(int(T2["nx"]), int(T2["nv"]), 0.5, T2["amplitude_below_kJ"])
     sim, f = sim_1d(f0, 1.0, 1.0, G=1.0)
     e0 = sim.energy()
     dE = dM = 0.0
@@ -196,8 +198,8 @@ def test_test2_energy_and_mass_conservation():
         dE = max(dE, abs(e["E"] - e0["E"]) / abs(e0["E"]))
         dM = max(dM, abs(e["M"] + e["M_out"] - e0["M"]) / e0["M"])
     sim.close()
-    assert dE < 1e-3
-    assert dM < 1e-6
+    assert dE < T2["energy_rel_bound"]
+    assert dM < T2["mass_rel_bound"]
 
 
 @pytest.mark.gpu
@@ -206,8 +208,10 @@ def test_test3_galilean_shift_at_landau_damping():
     (At v_t = 2 sigma the bound V = L/T cuts the shifted Maxwellian at 1.2
     sigma and the outflow changes the rate by a third in the oracle as well;
     that case is not a test of the scheme.)"""
-    f0, sigma, k = maxwell_1d(128, 128, 1.1, 0.1)
-    f1, _s, _k = maxwell_1d(128, 128, 1.1, 0.1, vt=sigma)
+    kk, nx, nv = T3["k_over_kJ"][1], int(T3["nx"]), int(T3["nv"])
+    amp = T2["amplitude_above_kJ"]
+    f0, sigma, k = maxwell_1d(nx, nv, kk, amp)
+    f1, _s, _k = maxwell_1d(nx, nv, kk, amp, vt=T3["vt_over_sigma"][0] * sigma)
     t0, a0 = run_gpu(f0, 1.01)
     t1, a1 = run_gpu(f1, 1.01)
     s0 = (t0 > 0.3) & (t0 < 1.0)

@@ -5,6 +5,8 @@ import math
 
 import numpy as np
 import pytest
+
+from conftest import golden
 from scipy.optimize import brentq
 from scipy.special import erfcx, erf
 
@@ -178,9 +180,22 @@ def test_energy_and_mass_conservation_test2():
     # Sec. 3.2: E within 1e-3 and M within 1e-6 (k/k_J = 0.5, 128 x 128),
     # checked up to t = 1.75 T; past 2 T the sheet that collapses is under-
     # resolved on 128 cells and the energy error grows past 1e-3
-    ts, amps, es, sigma, k = run_1d(0.5, 0.01, 128, 128, 1.75)
+    T2 = golden("paper_test2")
+    ts, amps, es, sigma, k = run_1d(0.5, T2["amplitude_below_kJ"], int(T2["nx"]), int(T2["nv"]),
+                                    1.75)
     E0, M0 = es[0][3], es[0][0]
     dE = max(abs(e[3] - E0) for e in es) / abs(E0)
     dM = max(abs(e[0] - M0) for e in es) / M0
-    assert dE < 1e-3
-    assert dM < 1e-6
+    assert dE < T2["energy_rel_bound"]
+    assert dM < T2["mass_rel_bound"]
+
+
+def test_white_noise_workloads_have_the_papers_jeans_wave_numbers():
+    """The Test 4 workloads (Sec. 3.4): rho_bar, G and sigma of the synthetic
+    boxes give the two Jeans wave numbers the paper prints."""
+    T4 = golden("paper_test4")
+    for kj_over_k1, kjl in zip((4.0, 8.0), T4["kJ_times_L_over_pi"]):
+        w = I.white_noise32(kj_over_k1)
+        L = w.box_hi[0] - w.box_lo[0]
+        kj = math.sqrt(4 * math.pi * w.G * w.rho_bar) / w.sigma
+        assert kj * L / math.pi == pytest.approx(kjl, rel=1e-12)
