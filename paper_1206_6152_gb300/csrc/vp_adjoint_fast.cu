@@ -590,7 +590,7 @@ __global__ void __launch_bounds__(128) k_adjoint_rows(const float *__restrict__ 
 // ran slower.)
 template <int N>
 struct KickZY {
-    static constexpr int P = N + 4, Q = N / 4, UPC = N * N / 32, WPC = 4;   // warps per CTA
+    static constexpr int P = N + 4, UPC = N * N / 32, WPC = 4;   // warps per CTA
     static constexpr size_t SMEM = (size_t)WPC * 3 * 32 * P * sizeof(float);
 };
 
