@@ -152,6 +152,19 @@ int vp_profile_step(vp_ctx *ctx, double *ms_out);
  * (graph kernel nodes times replays). */
 int vp_stats(vp_ctx *ctx, long long *kernels_launched);
 
+/* Scans the current f (one read; synchronises the stream): counts[0] =
+ * cells that are NaN or infinite, counts[1] = cells below zero (the scheme
+ * keeps f >= 0, Sec. 2.1); counts (host, 2 entries) may be NULL.  Returns
+ * VP_ERR_NONFINITE if either count is non-zero, else VP_OK. */
+int vp_check(vp_ctx *ctx, long long counts[2]);
+
+/* Fault injection for tests (not in the paper): the k-th device allocation
+ * the library's context set-up makes after this call fails as if the
+ * device were out of memory, so that the VP_ERR_OOM paths and their
+ * clean-up can be exercised without exhausting the device; k = 0 switches
+ * it off.  Process-wide; VP_ERR_ARG for k < 0. */
+int vp_debug_fail_alloc(int k);
+
 /* Discrete adjoint of one split step (not in the paper; limiter branches,
  * integer shifts and line-maximum positions frozen at the forward pass).
  * Requires dt_fixed > 0 (VP_ERR_STATE otherwise).  On first use the

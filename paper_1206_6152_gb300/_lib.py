@@ -21,7 +21,7 @@ EXPORTS = (
     "vp_moments", "vp_get_field", "vp_set_accel", "vp_energy", "vp_time", "vp_step_host",
     "vp_adjoint_step", "vp_field_adjoint", "vp_functional", "vp_destroy", "vp_error_string",
     "vp_profile_step", "vp_stats", "vp_sweep_adjoint", "vp_moments_noalloc",
-    "vp_set_adjoint_states",
+    "vp_set_adjoint_states", "vp_check", "vp_debug_fail_alloc",
 )
 PROFILE_SLOTS = 8
 PROFILE_NAMES = ("kick6", "drift_z", "drift_y", "drift_x", "density", "field", "tables", "step")
@@ -90,6 +90,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "vp_error_string": (ctypes.c_char_p, [i]),
             "vp_profile_step": (i, [vp, dp]),
             "vp_stats": (i, [vp, ctypes.POINTER(ctypes.c_longlong)]),
+            "vp_check": (i, [vp, ctypes.POINTER(ctypes.c_longlong)]),
+            "vp_debug_fail_alloc": (i, [i]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)

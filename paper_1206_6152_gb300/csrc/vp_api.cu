@@ -23,6 +23,8 @@
 #include <new>
 #include <vector>
 
+#include <atomic>
+
 #include "vp_device.cuh"
 #include "vp_internal.cuh"
 
@@ -31,6 +33,27 @@ namespace {
 thread_local char g_last_error[512];
 
 __global__ void k_set_scalar(double *p, double v) { *p = v; }
+
+// counts of the cells of f that are not finite (cnt[0]) and below zero (cnt[1])
+template <typename T>
+__global__ void k_check(const T *__restrict__ f, long long n, unsigned long long *cnt)
+{
+    unsigned long long bad = 0, neg = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const T v = f[i];
+        if (!isfinite(v)) ++bad;
+        else if (v < T(0)) ++neg;
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        bad += __shfl_xor_sync(0xffffffffu, bad, d);
+        neg += __shfl_xor_sync(0xffffffffu, neg, d);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (bad) atomicAdd(cnt, bad);
+        if (neg) atomicAdd(cnt + 1, neg);
+    }
+}
 __global__ void k_zero_lost(DevScalars *sc, double t0) { sc->lost = 0.0; sc->t = t0; sc->dt = 0.0; }
 
 template <typename T>
@@ -54,9 +77,14 @@ void free_ctx(vp_ctx *c)
     delete c;
 }
 
+// fault injection for tests: the k-th allocation after vp_debug_fail_alloc(k)
+// fails (0: off)
+std::atomic<int> g_fail_alloc{0};
+
 int dalloc(void **p, size_t bytes)
 {
     *p = nullptr;
+    if (g_fail_alloc.load() > 0 && g_fail_alloc.fetch_sub(1) == 1) return VP_ERR_OOM;
     cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -558,6 +586,34 @@ int vp_step_host(vp_ctx *c, const void *f_host_in, void *f_host_out, int nsteps,
                                 c->stream));
     VP_CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (t_out) *t_out = c->sc_host->t;
+    return VP_OK;
+}
+
+int vp_check(vp_ctx *c, long long *counts)
+{
+    if (!c) return VP_ERR_ARG;
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(c->red);
+    VP_CUDA_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), c->stream));
+    const unsigned grid = (unsigned)(vp_sm_count() * 8);
+    if (c->isdouble)
+        k_check<double><<<grid, 256, 0, c->stream>>>((const double *)c->f, c->ncells, cnt);
+    else
+        k_check<float><<<grid, 256, 0, c->stream>>>((const float *)c->f, c->ncells, cnt);
+    VP_CUDA_TRY(cudaGetLastError());
+    unsigned long long h[2];
+    VP_CUDA_TRY(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    VP_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (counts) {
+        counts[0] = (long long)h[0];
+        counts[1] = (long long)h[1];
+    }
+    return (h[0] || h[1]) ? VP_ERR_NONFINITE : VP_OK;
+}
+
+int vp_debug_fail_alloc(int k)
+{
+    if (k < 0) return VP_ERR_ARG;
+    g_fail_alloc.store(k);
     return VP_OK;
 }
 

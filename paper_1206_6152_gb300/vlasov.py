@@ -149,6 +149,14 @@ class VlasovPoisson:
         check(self.lib.vp_profile_step(self._ctx, out), "vp_profile_step")
         return dict(zip(_lib.PROFILE_NAMES, list(out)))
 
+    def check(self) -> Tuple[int, int]:
+        """(cells of f that are NaN or infinite, cells below zero)."""
+        out = (ctypes.c_longlong * 2)()
+        code = self.lib.vp_check(self._ctx, out)
+        if code not in (0, -4):
+            check(code, "vp_check")
+        return int(out[0]), int(out[1])
+
     def kernels_launched(self) -> int:
         n = ctypes.c_longlong()
         check(self.lib.vp_stats(self._ctx, ctypes.byref(n)), "vp_stats")

@@ -68,3 +68,9 @@ def test_invalid_config_rejected_before_cuda(lib, bad):
     # a fake non-null pointer: the configuration check runs before any use
     assert lib.vp_init(ctypes.byref(cfg), ctypes.c_void_p(16), None, ctypes.byref(ctx)) == -1
     assert not ctx.value
+
+
+def test_fault_injection_switch(lib):
+    assert lib.vp_debug_fail_alloc(-1) == -5
+    assert lib.vp_debug_fail_alloc(0) == 0
+    assert lib.vp_check(None, None) == -5

@@ -310,6 +310,47 @@ def test_error_codes():
 
 
 @pytest.mark.gpu
+def test_check_counts_non_finite_and_negative_cells():
+    """vp_check on a valid f and on one with planted faults (host-side
+    injection: the values are written into f before the scan)."""
+    w = I.small_maxwell(dtype="f32")
+    sim, f = gpu_sim(w, I.initial_condition(w))
+    assert sim.check() == (0, 0)
+    sim.step(2)
+    assert sim.check() == (0, 0)                # the scheme keeps f >= 0
+    flat = f.view(-1)
+    flat[7] = float("nan")
+    flat[11] = float("inf")
+    flat[13] = -1e-3
+    assert sim.check() == (2, 1)
+    sim.close()
+
+
+@pytest.mark.gpu
+def test_injected_allocation_failure_is_reported_and_cleaned_up():
+    """An allocation made to fail during context set-up: vp_init reports
+    VP_ERR_OOM and frees what it had allocated; the next set-up succeeds."""
+    from paper_1206_6152_gb300 import _lib
+    from paper_1206_6152_gb300.vlasov import VlasovPoisson, config_of
+    w = I.small_maxwell(dtype="f64")
+    f = torch.from_numpy(I.initial_condition(w)).to(DEV)
+    lib = _lib.load()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for k in (1, 3, 6):
+        assert lib.vp_debug_fail_alloc(k) == 0
+        with pytest.raises(_lib.VPError) as ei:
+            VlasovPoisson(config_of(w), f)
+        assert ei.value.code == -2
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) < (64 << 20)
+    lib.vp_debug_fail_alloc(0)
+    sim = VlasovPoisson(config_of(w), f)
+    sim.step(1)
+    sim.close()
+
+
+@pytest.mark.gpu
 @pytest.mark.slow
 def test_jeans_32_full_size_two_steps():
     """The 32^3 x 32^3 FP32 Jeans workload at full size, in the launch
