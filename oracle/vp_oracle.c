@@ -30,7 +30,7 @@
  * in its ratio form  eps = min(1, 2 f / (f_{j+1} - f_j))  etc.; the paper
  * cites it without printing it.
  *
- * Readings where the paper is silent (each also listed in the design doc):
+ * Readings where the paper is silent:
  *   - the line maximum f_inf is the maximum of f over the in-domain cells
  *     of the line being swept, taken at t^n;
  *   - outflow ghost cells hold f = 0 and their own partial integral is

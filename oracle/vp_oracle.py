@@ -18,7 +18,7 @@ What it computes, in the paper's order (Yoshikawa, Yoshida & Umemura 2013):
   * Sec. 3.1 / 3.2: diagnostics M, K, U, E.
 numpy's FFT serves as the FFT step.
 
-Readings where the paper is silent or garbled (also listed in the design doc):
+Readings where the paper is silent or garbled:
   * G(k = 0) = 0 (the mean density does not source the periodic potential);
   * for unequal spacings the periodic Green's function is the one of the same
     7-point Laplacian, -pi G / sum_l sin^2(k_l D_l / 2) / D_l^2;
