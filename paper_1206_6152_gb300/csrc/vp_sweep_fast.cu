@@ -677,12 +677,14 @@ __global__ void __launch_bounds__(128, N <= 32 ? 4 : 1) k_drift_fast(const T *__
 }
 
 // ---------------------------------------------------------------------------
-// fused z and y drift (FP32, N_y = N_z = N): one CTA per (x, chunk of VC
-// velocity cells).  The CTA's block [y][z][VC] is copied into a shared tile
-// with 16-byte cp.async copies; the z sweep takes its lines (pairs of
-// adjacent velocity cells) from the tile and writes them back in place; the
-// y sweep reads its lines from the tile and writes them straight to global
-// memory.  f crosses HBM once for both sweeps.  The chunk lies inside one vz
+// fused z and y drift (FP32, N_y = N_z = N): a block is (x, chunk of VC
+// velocity cells); persistent CTAs take blocks in turn.  A block [y][z][VC]
+// is copied into a shared tile with 16-byte cp.async copies; the z sweep
+// takes its lines (pairs of adjacent velocity cells) from the tile and
+// writes them back in place; the y sweep reads its lines from the tile into
+// registers, the copies of the CTA's next block start, and the y lines are
+// swept and written straight to global memory.  f crosses HBM once for both
+// sweeps.  The chunk lies inside one vz
 // row, so every y line of the CTA has the same v_y; the z lines of a pair
 // differ in v_z (two coefficients, two scalar lines where the pair
 // straddles the sign change of v_z).
@@ -701,7 +703,7 @@ __global__ void __launch_bounds__(DriftYZ<N>::NT, 2) k_drift_yz(const float *__r
                                                               const LineCoef<float> *__restrict__ cz,
                                                               const LineCoef<float> *__restrict__ cy,
                                                               long long nvc, int nvy, int nvz,
-                                                              double *lost_out,
+                                                              long long nblocks, double *lost_out,
                                                               float *__restrict__ fo)
 {
     constexpr int VC = DriftYZ<N>::VC, YP = DriftYZ<N>::YP, H = VC / 2;
@@ -709,16 +711,14 @@ __global__ void __launch_bounds__(DriftYZ<N>::NT, 2) k_drift_yz(const float *__r
     float *tile = reinterpret_cast<float *>(smem_raw);
     __shared__ Acc<double> red[32];
     const int t = threadIdx.x, vp = t % H, r = t / H;    // r: y in the z sweep, z in the y sweep
-    const long long v0 = (long long)blockIdx.x * VC;
-    const long long x0 = (long long)blockIdx.y * N * N;  // first spatial cell of the x plane
-    const long long v = v0 + 2 * vp;
+    const long long nvb = nvc / VC;                      // velocity blocks per x plane
     float lost = 0.f;
-    float2 x[N];
-    // the CTA's block [y][z][VC] into the tile with asynchronous 16-byte
-    // copies (no register staging, few load instructions)
-    {
+    // block b = (x plane b / nvb, velocity cells [VC (b % nvb), + VC)) into
+    // the tile [y][z][VC] with asynchronous 16-byte copies (no register
+    // staging, few load instructions)
+    auto stage = [&](long long b) {
         constexpr int Q = VC / 4, PIECES = N * N * Q;
-        const float *src = f + x0 * nvc + v0;
+        const float *src = f + (b / nvb) * N * N * nvc + (b % nvb) * VC;
 #pragma unroll 4
         for (int e = t; e < PIECES; e += DriftYZ<N>::NT) {
             const int q = e % Q, yz = e / Q, y = yz / N, z = yz % N;
@@ -727,33 +727,47 @@ __global__ void __launch_bounds__(DriftYZ<N>::NT, 2) k_drift_yz(const float *__r
                          "l"(src + (long long)yz * nvc + 4 * q)
                          : "memory");
         }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if ((long long)blockIdx.x < nblocks) stage(blockIdx.x);
+    for (long long b = blockIdx.x; b < nblocks; b += gridDim.x) {
+        const long long v0 = (b % nvb) * VC;
+        const long long x0 = (b / nvb) * N * N;          // first spatial cell of the x plane
+        const long long v = v0 + 2 * vp;
+        float2 x[N];
         asm volatile("cp.async.wait_all;" ::: "memory");
-    }
-    __syncthreads();
-    {
-        // z sweep of the line (y = r, v pair), in place in the tile
-        float *q = tile + r * YP + 2 * vp;
+        __syncthreads();
+        {
+            // z sweep of the line (y = r, v pair), in place in the tile
+            float *q = tile + r * YP + 2 * vp;
 #pragma unroll
-        for (int j = 0; j < N; ++j) x[j] = *reinterpret_cast<const float2 *>(q + j * VC);
-        const LineCoef<float> ca = cz[(int)(v % nvz)], cb = cz[(int)((v + 1) % nvz)];
-        lost += drift_pair<N, PERIODIC>(x, ca, cb);
+            for (int j = 0; j < N; ++j) x[j] = *reinterpret_cast<const float2 *>(q + j * VC);
+            const LineCoef<float> ca = cz[(int)(v % nvz)], cb = cz[(int)((v + 1) % nvz)];
+            lost += drift_pair<N, PERIODIC>(x, ca, cb);
 #pragma unroll
-        for (int j = 0; j < N; ++j) *reinterpret_cast<float2 *>(q + j * VC) = x[j];
-    }
-    __syncthreads();
-    {
-        const float *q = tile + r * VC + 2 * vp;
+            for (int j = 0; j < N; ++j) *reinterpret_cast<float2 *>(q + j * VC) = x[j];
+        }
+        __syncthreads();
+        {
+            const float *q = tile + r * VC + 2 * vp;
 #pragma unroll
-        for (int j = 0; j < N; ++j) x[j] = *reinterpret_cast<const float2 *>(q + j * YP);
-        const LineCoef<float> c = cy[(int)((v0 / nvz) % nvy)];
-        lost += drift_pair<N, PERIODIC>(x, c, c);
-        float *p = fo + (x0 + r) * nvc + v;
-        const long long ys = (long long)N * nvc;
+            for (int j = 0; j < N; ++j) x[j] = *reinterpret_cast<const float2 *>(q + j * YP);
+        }
+        // every line of the y sweep is in registers: the next block's copies
+        // into the tile run under this block's y sweep and stores
+        __syncthreads();
+        if (b + gridDim.x < nblocks) stage(b + gridDim.x);
+        {
+            const LineCoef<float> c = cy[(int)((v0 / nvz) % nvy)];
+            lost += drift_pair<N, PERIODIC>(x, c, c);
+            float *p = fo + (x0 + r) * nvc + v;
+            const long long ys = (long long)N * nvc;
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-            *reinterpret_cast<float2 *>(p) = x[j];
-            p += ys;
-            asm volatile("" : "+l"(p));
+            for (int j = 0; j < N; ++j) {
+                *reinterpret_cast<float2 *>(p) = x[j];
+                p += ys;
+                asm volatile("" : "+l"(p));
+            }
         }
     }
     if (!PERIODIC) {
@@ -769,21 +783,21 @@ cudaError_t drift_yz_n(vp_ctx *c, const float *f, const LineCoef<float> *coef, f
 {
     constexpr int NT = DriftYZ<N>::NT;
     const size_t smem = (size_t)N * DriftYZ<N>::YP * sizeof(float);
-    const dim3 grid((unsigned)(c->nvc / DriftYZ<N>::VC), (unsigned)c->n[0]);
+    const long long nblocks = (c->nvc / DriftYZ<N>::VC) * (long long)c->n[0];
     const LineCoef<float> *cz = coef + (size_t)2 * c->maxnv, *cy = coef + (size_t)c->maxnv;
-    if (c->periodic_space) {
-        cudaError_t e = cudaFuncSetAttribute(k_drift_yz<N, true>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_drift_yz<N, true><<<grid, NT, smem, c->stream>>>(f, cz, cy, c->nvc, c->nv[1], c->nv[2],
-                                                           &c->sc->lost, fo);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(k_drift_yz<N, false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_drift_yz<N, false><<<grid, NT, smem, c->stream>>>(f, cz, cy, c->nvc, c->nv[1], c->nv[2],
-                                                            &c->sc->lost, fo);
-    }
+    auto kern = c->periodic_space ? k_drift_yz<N, true> : k_drift_yz<N, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // persistent: the CTAs that fit on the GPU at once, each taking blocks
+    // in turn
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    long long grid = (long long)per_sm * vp_sm_count();
+    if (grid > nblocks) grid = nblocks;
+    kern<<<(unsigned)grid, NT, smem, c->stream>>>(f, cz, cy, c->nvc, c->nv[1], c->nv[2], nblocks,
+                                                  &c->sc->lost, fo);
     return cudaGetLastError();
 }
 
