@@ -31,6 +31,8 @@ from .vlasov import VlasovPoisson
 
 
 def _free_bytes(dev: torch.device) -> int:
+    if dev.type != "cuda":
+        return 1 << 62          # host tensors: no device-memory limit applies
     free, _total = torch.cuda.mem_get_info(dev)
     return free
 
