@@ -9,6 +9,33 @@ from oracle import vp_oracle as O
 from paper_1206_6152_gb300 import inputs as I
 
 
+def limiter_arms(f, alpha, periodic):
+    """The branch pattern of one line update, restated on the test side from
+    the corrector's case split (Filbet et al. 2001, ratio form): for every
+    cell of the line in upwind order, which arm each corrected difference
+    takes (0: unlimited, 1: limited by the positivity bound, 2: limited by
+    the maximum bound), and the first position of the line maximum.  A
+    central difference is a valid check of the frozen-branch adjoint only if
+    both of its runs keep the pattern of the unperturbed line."""
+    g = np.asarray(f, dtype=np.float64)[::-1] if alpha < 0 else np.asarray(f, dtype=np.float64)
+    n = g.size
+    finf = max(float(g.max()), 0.0)
+
+    def cell(j):
+        if periodic:
+            return g[j % n]
+        return g[j] if 0 <= j < n else 0.0
+
+    pattern = []
+    for j in range(n):
+        fm, f0, fp = cell(j - 1), cell(j), cell(j + 1)
+        dp, dm = fp - f0, f0 - fm
+        ap = 1 if dp > 0 and 2 * f0 < dp else (2 if dp < 0 and 2 * (finf - f0) < -dp else 0)
+        am = 2 if dm > 0 and 2 * (finf - f0) < dm else (1 if dm < 0 and 2 * f0 < -dm else 0)
+        pattern.append((ap, am))
+    return pattern, int(np.argmax(g))
+
+
 @pytest.mark.parametrize("periodic", [True, False])
 @pytest.mark.parametrize("alpha", [0.23, 0.81, 1.37, -0.44, -2.61])
 def test_line_adjoint_matches_fd(periodic, alpha):
@@ -19,13 +46,17 @@ def test_line_adjoint_matches_fd(periodic, alpha):
     w = rng.normal(size=n)
     lam, dalpha = O.pfc_line_adjoint(f, w, alpha, periodic)
     h = 1e-7
+    arms = limiter_arms(f, alpha, periodic)
+    assert any(a != (0, 0) for a in arms[0])      # the line exercises the corrector
     for j in range(n):
         e = np.zeros(n)
         e[j] = h
         if f[j] == 0.0:                # one-sided: f >= 0
+            assert limiter_arms(f + e, alpha, periodic) == arms
             fd = (w @ O.pfc_line(f + e, alpha, periodic) - w @ O.pfc_line(f, alpha, periodic)) / h
             assert lam[j] == pytest.approx(fd, rel=1e-5, abs=1e-6)
             continue
+        assert limiter_arms(f + e, alpha, periodic) == arms == limiter_arms(f - e, alpha, periodic)
         fd = (w @ O.pfc_line(f + e, alpha, periodic) - w @ O.pfc_line(f - e, alpha, periodic)) / (2 * h)
         assert lam[j] == pytest.approx(fd, rel=1e-6, abs=1e-7)
     fd = (w @ O.pfc_line(f, alpha + h, periodic) - w @ O.pfc_line(f, alpha - h, periodic)) / (2 * h)
