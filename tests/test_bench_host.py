@@ -57,3 +57,12 @@ def test_aggregate_is_cells_over_the_slowest_rank():
             return x
     ms, value = bench.aggregate(8.0, 1.0e9, 10, One())
     assert ms == 8.0 and value == pytest.approx(1.0e9 * 10 / 8e-3)
+
+
+def test_reference_steps_sample_the_density():
+    w = I.small_maxwell(n=(8, 4, 4), nv=(8, 8, 8), dtype="f64", amp=0.2)
+    f0 = I.initial_condition(w)
+    rho = bench.oracle_density(w, f0)
+    assert rho.shape == tuple(w.n)
+    rate, full, desc = bench.oracle_step_rate(w, f0, 0.25, rho)
+    assert rate > 0 and "density timed on 2 of 8 x planes" in desc
