@@ -160,6 +160,12 @@ class Clocks:
 # CPU oracle (test infrastructure): bounded sample of one split step
 # ---------------------------------------------------------------------------
 
+def oracle_threads() -> int:
+    """Threads the oracle's OpenMP loops run on."""
+    from oracle import vp_oracle as O
+    return O.threads()
+
+
 def oracle_density(w, f0_np):
     """The oracle's density of the whole grid, slab by slab."""
     import numpy as np
@@ -392,7 +398,7 @@ def run_ours(args, ranks: Ranks):
     cpu = None
     if ranks.rank == 0 and ranks.world == 1 and not args.no_cpu_baseline and f0 is not None:
         rate, full_s, desc = oracle_step_rate(w, f0, args.cpu_sample)
-        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+        cpu = {"value": rate, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
                "sample": desc}
 
     out = {
@@ -495,7 +501,7 @@ def run_reference(args, ranks: Ranks):
         fulls.append(full)
     ms = 1e3 * statistics.mean(fulls)
     value = w.cells / (ms / 1e3)
-    cpu = {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+    cpu = {"value": value, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
            "sample": desc}
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,

@@ -46,6 +46,7 @@
  * as inactive.
  */
 #include <math.h>
+#include <omp.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -437,3 +438,6 @@ void oracle_moments(const double *f, long np, long nv, const double *v2,
     out[0] = s0 + c0;
     out[1] = s2 + c2;
 }
+
+/* Number of threads the OpenMP loops above run on (for reporting). */
+int oracle_threads(void) { return omp_get_max_threads(); }

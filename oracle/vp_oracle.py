@@ -89,8 +89,15 @@ def lib():
             L.oracle_density.restype = None
             L.oracle_moments.argtypes = [dp, ctypes.c_long, ctypes.c_long, dp, dp]
             L.oracle_moments.restype = None
+            L.oracle_threads.argtypes = []
+            L.oracle_threads.restype = ctypes.c_int
             _lib = L
     return _lib
+
+
+def threads() -> int:
+    """Threads the oracle's parallel loops run on."""
+    return int(lib().oracle_threads())
 
 
 def _dptr(a: np.ndarray):

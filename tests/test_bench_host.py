@@ -66,3 +66,9 @@ def test_reference_steps_sample_the_density():
     assert rho.shape == tuple(w.n)
     rate, full, desc = bench.oracle_step_rate(w, f0, 0.25, rho)
     assert rate > 0 and "density timed on 2 of 8 x planes" in desc
+
+
+def test_cores_are_the_oracles_openmp_threads():
+    from oracle import vp_oracle as O
+    n = bench.oracle_threads()
+    assert n == O.threads() and 1 <= n <= (os.cpu_count() or n)
