@@ -46,3 +46,32 @@ def test_two_rank_aggregation():
         ms, value = out[r]
         assert ms == pytest.approx(20.0)                     # slowest rank
         assert value == pytest.approx(world * 1000.0 * 5 / 0.020)
+
+
+def _ref_worker(rank, world, port, out):
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank),
+                      MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    sys.argv = ["bench.py", "--impl", "reference", "--workload", "landau16_f64", "--steps", "1",
+                "--warmup", "0"]
+    import bench
+    ranks = bench.Ranks()
+    try:
+        res = bench.run_reference(bench.parse(), ranks)
+        out[rank] = None if res is None else (res["impl"], res["value"], res["cpu_baseline"]["kind"])
+    finally:
+        ranks.close()
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="CPU gloo check")
+def test_reference_arm_runs_on_rank_0_only():
+    """Under torchrun the reference arm (the oracle) runs on rank 0 alone; the
+    other ranks return at once without work."""
+    world = 2
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.spawn(_ref_worker, args=(world, port, out), nprocs=world, join=True)
+    assert out[1] is None
+    impl, value, kind = out[0]
+    assert impl == "reference" and kind == "oracle" and value > 0
