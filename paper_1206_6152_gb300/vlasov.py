@@ -98,7 +98,37 @@ class VlasovPoisson:
     def sweep(self, axis: int, tau: float) -> None:
         check(self.lib.vp_sweep(self._ctx, int(axis), float(tau)), "vp_sweep")
 
+    # -- argument checks: the library dereferences the pointers on the GPU,
+    # so a tensor of the wrong kind is refused here rather than read there
+    def _state(self, t: torch.Tensor, name: str) -> torch.Tensor:
+        """A contiguous tensor of f's shape and dtype on f's device."""
+        if (not isinstance(t, torch.Tensor) or t.device != self.device or t.dtype != self.f.dtype
+                or tuple(t.shape) != tuple(self.f.shape) or not t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous {self.f.dtype} tensor of shape "
+                             f"{tuple(self.f.shape)} on {self.device}")
+        return t
+
+    def _host_state(self, t: torch.Tensor, name: str) -> torch.Tensor:
+        """A contiguous host tensor of f's shape and dtype."""
+        if (not isinstance(t, torch.Tensor) or t.device.type != "cpu" or t.dtype != self.f.dtype
+                or tuple(t.shape) != tuple(self.f.shape) or not t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous host {self.f.dtype} tensor of shape "
+                             f"{tuple(self.f.shape)}")
+        return t
+
+    def _field_arg(self, t: torch.Tensor, k: int, name: str) -> torch.Tensor:
+        """A contiguous float64 tensor of shape (k, Nx, Ny, Nz) (k = 1: (Nx, Ny, Nz))
+        on f's device."""
+        n = tuple(self.cfg.n)
+        shape = n if k == 1 else (k,) + n
+        if (not isinstance(t, torch.Tensor) or t.device != self.device
+                or t.dtype != torch.float64 or tuple(t.shape) != shape or not t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous float64 tensor of shape {shape} on "
+                             f"{self.device}")
+        return t
+
     def set_distribution(self, f: torch.Tensor) -> None:
+        self._state(f, "f")
         check(self.lib.vp_set_distribution(self._ctx, _ptr(f)), "vp_set_distribution")
         self.f = f
 
@@ -121,7 +151,7 @@ class VlasovPoisson:
         return rho, phi, g
 
     def set_accel(self, g: torch.Tensor) -> None:
-        g = g.to(device=self.device, dtype=torch.float64).contiguous()
+        g = self._field_arg(g.to(device=self.device, dtype=torch.float64).contiguous(), 3, "g")
         check(self.lib.vp_set_accel(self._ctx, _ptr(g)), "vp_set_accel")
         self._keep = g
 
@@ -137,6 +167,9 @@ class VlasovPoisson:
 
     def step_host(self, f_host_in: torch.Tensor, nsteps: int, f_host_out: Optional[torch.Tensor] = None,
                   diagnostics: bool = False):
+        self._host_state(f_host_in, "f_host_in")
+        if f_host_out is not None:
+            self._host_state(f_host_out, "f_host_out")
         t = ctypes.c_double()
         diag = (ctypes.c_double * 5)() if diagnostics else None
         check(self.lib.vp_step_host(self._ctx, _ptr(f_host_in), _ptr(f_host_out), int(nsteps),
@@ -165,6 +198,10 @@ class VlasovPoisson:
     # -- adjoint ----------------------------------------------------------
     def adjoint_step(self, f_start: torch.Tensor, g_start: torch.Tensor, lam_f: torch.Tensor,
                      lam_g: torch.Tensor) -> None:
+        self._state(f_start, "f_start")
+        self._field_arg(g_start, 3, "g_start")
+        self._state(lam_f, "lam_f")
+        self._field_arg(lam_g, 3, "lam_g")
         check(self.lib.vp_adjoint_step(self._ctx, _ptr(f_start), _ptr(g_start), _ptr(lam_f),
                                        _ptr(lam_g)), "vp_adjoint_step")
 
@@ -175,13 +212,22 @@ class VlasovPoisson:
 
     def sweep_adjoint(self, axis: int, tau: float, f_in: torch.Tensor, lam: torch.Tensor,
                       lam_g: Optional[torch.Tensor] = None) -> None:
+        self._state(f_in, "f_in")
+        self._state(lam, "lam")
+        if lam_g is not None:
+            self._field_arg(lam_g, 3, "lam_g")
         check(self.lib.vp_sweep_adjoint(self._ctx, int(axis), float(tau), _ptr(f_in), _ptr(lam),
                                         _ptr(lam_g)), "vp_sweep_adjoint")
 
     def field_adjoint(self, lam_g: torch.Tensor, lam_f: torch.Tensor) -> None:
+        self._field_arg(lam_g, 3, "lam_g")
+        self._state(lam_f, "lam_f")
         check(self.lib.vp_field_adjoint(self._ctx, _ptr(lam_g), _ptr(lam_f)), "vp_field_adjoint")
 
     def functional(self, kind: int, lam_f: torch.Tensor, target: Optional[torch.Tensor] = None) -> float:
+        self._state(lam_f, "lam_f")
+        if target is not None:
+            self._field_arg(target, 1, "target")
         J = ctypes.c_double()
         check(self.lib.vp_functional(self._ctx, int(kind), _ptr(target), _ptr(lam_f), ctypes.byref(J)),
               "vp_functional")
