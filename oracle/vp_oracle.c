@@ -99,9 +99,10 @@ static double eps_minus_diff(double fm, double f0, double finf)
 }
 
 /* Integral of the corrected third-order reconstruction of f over the
- * rightmost fraction beta of cell j, divided by dx.  For beta in [0,1]
- * this is the piece of Phi at the right face of cell j contributed by
- * cell j itself. */
+ * rightmost fraction beta of cell j, divided by dx (Sec. 2.1: the
+ * reconstruction with Filbet's slope corrector that the fluxes of
+ * Eqs. (phi_plus), (phi_minus) integrate).  For beta in [0,1] this is the
+ * piece of Phi at the right face of cell j contributed by cell j itself. */
 static double partial_integral(const double *f, long n, long j, double beta,
                                double finf, int periodic)
 {
@@ -114,8 +115,8 @@ static double partial_integral(const double *f, long n, long j, double beta,
                      + wm * eps_minus_diff(fm, f0, finf);
 }
 
-/* Phi at the right face of cell i (i.e. at x_{i+1/2}) for a shift
- * alpha = u dt / dx = s + beta >= 0: the foot of the characteristic
+/* Phi at the right face of cell i (i.e. at x_{i+1/2}), Eq. (phi_plus), for
+ * a shift alpha = u dt / dx = s + beta >= 0: the foot of the characteristic
  * through x_{i+1/2} lies a fraction beta from the right face of cell
  * i - s, so Phi = (whole cells i-s+1 .. i) + (part of cell i-s). */
 static double face_flux(const double *f, long n, long i, long s, double beta,
@@ -127,7 +128,9 @@ static double face_flux(const double *f, long n, long i, long s, double beta,
     return phi;
 }
 
-/* Forward PFC update of one line with alpha >= 0. */
+/* Forward PFC update of one line with alpha >= 0 (Sec. 2.1, Eq. (conserve)
+ * as f_i + Phi^- - Phi^+, the line maximum taken at t^n); a rounding-negative
+ * result is set to 0. */
 static void pfc_line_pos(const double *f, double *out, long n, double alpha,
                          int periodic)
 {
@@ -143,7 +146,8 @@ static void pfc_line_pos(const double *f, double *out, long n, double alpha,
     }
 }
 
-/* Public: one line, any sign of alpha.  fin and fout may alias. */
+/* Public: one line, any sign of alpha (u < 0 as the mirror image of u > 0,
+ * Sec. 2.1).  fin and fout may alias. */
 void oracle_pfc_line(const double *fin, double *fout, long n, double alpha,
                      int periodic)
 {
@@ -195,7 +199,8 @@ static void eps_minus_diff_adj(double fm, double f0, double finf, double c,
     }
 }
 
-/* Index of an in-domain cell after the ghost rule, or -1 for a ghost. */
+/* Index of an in-domain cell after the ghost rule of Sec. 2.1, or -1 for a
+ * ghost. */
 static long cell_index(long n, long j, int periodic)
 {
     if (periodic) {
@@ -212,7 +217,8 @@ static void add_at(double *lam, long n, long j, int periodic, double v)
     if (m >= 0) lam[m] += v;
 }
 
-/* Reverse of partial_integral: cotangent psi of P_j(beta).  Returns the
+/* Reverse of partial_integral (the adjoint is not in the paper; the arms
+ * of the corrector are frozen): cotangent psi of P_j(beta).  Returns the
  * contribution psi * dP_j/dbeta. */
 static double partial_integral_adj(const double *f, long n, long j,
                                    double beta, double finf, int periodic,
@@ -237,8 +243,10 @@ static double partial_integral_adj(const double *f, long n, long j,
     return psi * (f0 + dwp * ep + dwm * em);
 }
 
-/* Adjoint of pfc_line_pos: lout = cotangent of out, lin = cotangent of f
- * (overwritten).  Returns dJ/dalpha. */
+/* Adjoint of pfc_line_pos (not in the paper; frozen arms, the rounding
+ * guard inactive, the line-maximum cotangent to its first position):
+ * lout = cotangent of out, lin = cotangent of f (overwritten).  Returns
+ * dJ/dalpha. */
 static double pfc_line_pos_adj(const double *f, const double *lout,
                                double *lin, long n, double alpha, int periodic)
 {
@@ -363,8 +371,9 @@ double oracle_sweep(double *f, const long dims[6], int axis,
     return lost;
 }
 
-/* Adjoint of oracle_sweep at input fin.  lam: cotangent of the output on
- * entry, of the input on exit.  dspeed (may be NULL) accumulates dJ/du. */
+/* Adjoint of oracle_sweep at input fin (not in the paper; frozen arms).
+ * lam: cotangent of the output on entry, of the input on exit.  dspeed (may
+ * be NULL) accumulates dJ/du. */
 void oracle_sweep_adjoint(const double *fin, double *lam, const long dims[6],
                           int axis, const double *speed, double tau, double h,
                           int periodic, double *dspeed)
@@ -421,9 +430,10 @@ void oracle_density(const double *f, long np, long nv, double dvol,
     }
 }
 
-/* Sums of f and of f |v|^2 over the whole array (unscaled); v2[v] is
- * |v|^2 at the cell centre of velocity cell v.  out[0] = sum f,
- * out[1] = sum f v^2. */
+/* Sums of f and of f |v|^2 over the whole array (unscaled; the M and K of
+ * Sec. 3.1, Eqs. (total_mass), (kinetic_energy), before the volume
+ * factors); v2[v] is |v|^2 at the cell centre of velocity cell v.
+ * out[0] = sum f, out[1] = sum f v^2. */
 void oracle_moments(const double *f, long np, long nv, const double *v2,
                     double *out)
 {

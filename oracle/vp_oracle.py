@@ -134,9 +134,11 @@ def _dims(f: np.ndarray):
 
 def sweep(f: np.ndarray, axis: int, speed: np.ndarray, tau: float, h: float,
           periodic: bool) -> float:
-    """T_axis(tau) in place on f[x][y][z][vx][vy][vz].  speed: cell-centre
-    velocities (position axis) or accelerations on the spatial grid (velocity
-    axis).  Returns the phase-space sum of f that left through outflow faces."""
+    """T_axis(tau) in place on f[x][y][z][vx][vy][vz] (Sec. 2.1, Eqs.
+    (adv_xpos)-(adv_zvel): the 1D update applied to every line along the
+    axis).  speed: cell-centre velocities (position axis) or accelerations on
+    the spatial grid (velocity axis).  Returns the phase-space sum of f that
+    left through outflow faces."""
     sp = np.ascontiguousarray(speed, dtype=np.float64).reshape(-1)
     return lib().oracle_sweep(_dptr(f), _dims(f), int(axis), _dptr(sp), float(tau), float(h),
                               int(bool(periodic)))
@@ -144,6 +146,10 @@ def sweep(f: np.ndarray, axis: int, speed: np.ndarray, tau: float, h: float,
 
 def sweep_adjoint(fin: np.ndarray, lam: np.ndarray, axis: int, speed: np.ndarray, tau: float,
                   h: float, periodic: bool, dspeed: Optional[np.ndarray] = None) -> None:
+    """Frozen-branch adjoint of `sweep` (not in the paper): lam (the
+    cotangent of the sweep's output) is replaced by that of its input fin;
+    with dspeed, the derivative with respect to each line's speed is added
+    there (one entry per spatial cell for a velocity axis)."""
     sp = np.ascontiguousarray(speed, dtype=np.float64).reshape(-1)
     dp = None
     if dspeed is not None:
@@ -159,6 +165,8 @@ def sweep_adjoint(fin: np.ndarray, lam: np.ndarray, axis: int, speed: np.ndarray
 
 @dataclasses.dataclass
 class Grid:
+    """The phase-space grid of Sec. 2: N_x N_y N_z cells on [lo, hi) and
+    N^v cells per velocity axis on [V^-, V^+), values as cell averages."""
     n: Tuple[int, int, int]
     nv: Tuple[int, int, int]
     lo: Tuple[float, float, float]
@@ -197,6 +205,8 @@ class Grid:
 # ---------------------------------------------------------------------------
 
 def density(f: np.ndarray, grid: Grid) -> np.ndarray:
+    """rho(x) = sum over velocity cells of f dv_x dv_y dv_z (Sec. 2.2),
+    compensated."""
     np_ = int(np.prod(grid.n))
     nv = int(np.prod(grid.nv))
     rho = np.empty(np_)
@@ -205,7 +215,9 @@ def density(f: np.ndarray, grid: Grid) -> np.ndarray:
 
 
 def green_periodic(grid: Grid, G: float) -> np.ndarray:
-    """Discrete Green's function of the 7-point Laplacian in k space."""
+    """Green's function of the periodic solve in k space (Sec. 2.2): the
+    discrete one of the 7-point Laplacian, -pi G / sum_l sin^2(k_l dx_l / 2)
+    / dx_l^2, and 0 at k = 0."""
     s = np.zeros(grid.n)
     for a in range(3):
         m = np.fft.fftfreq(grid.n[a]) * grid.n[a]          # integer wave numbers
@@ -248,8 +260,9 @@ def green_isolated(grid: Grid, G: float) -> np.ndarray:
 
 def poisson(rho: np.ndarray, grid: Grid, G: float, bc: str,
             ghat: Optional[np.ndarray] = None) -> np.ndarray:
-    """phi from rho.  Periodic: phi = IFFT(G(k) FFT(rho)).  Isolated: the
-    doubled-grid convolution; returns phi on the whole 2N grid."""
+    """phi from rho by FFT convolution (Sec. 2.2).  Periodic: phi =
+    IFFT(G(k) FFT(rho)).  Isolated: Hockney's doubled-grid convolution with
+    the -G/r kernel; returns phi on the whole 2N grid."""
     if bc == "periodic":
         gk = green_periodic(grid, G) if ghat is None else ghat
         return np.real(np.fft.ifftn(gk * np.fft.fftn(rho)))
@@ -275,6 +288,7 @@ def force(phi: np.ndarray, grid: Grid, bc: str) -> np.ndarray:
 
 
 def potential_in_box(phi: np.ndarray, grid: Grid) -> np.ndarray:
+    """The part of phi on the physical box (the whole array when periodic)."""
     return phi[:grid.n[0], :grid.n[1], :grid.n[2]]
 
 
@@ -295,6 +309,8 @@ def timestep(g: np.ndarray, grid: Grid, courant: float) -> float:
 
 @dataclasses.dataclass
 class Params:
+    """G, the Courant number C (Sec. 2.4), a fixed dt (> 0) or adaptive, and
+    the boundary rules of Sec. 2.1 (position sweeps) and Sec. 2.2 (Poisson)."""
     G: float = 1.0
     courant: float = 0.5
     dt_fixed: float = 0.0
@@ -307,7 +323,9 @@ class Params:
 
 
 class Simulation:
-    """f (FP64) with its acceleration g; `step` is one split step."""
+    """f (FP64) with its acceleration g; `step` is one split step of
+    Eq. (integration), read right to left: half kick vx, vy, vz with g^n,
+    drift z, y, x, field of the drifted f, half kick with g^{n+1}."""
 
     def __init__(self, f: np.ndarray, grid: Grid, params: Params):
         self.grid = grid
@@ -321,21 +339,25 @@ class Simulation:
         self.rho, self.phi, self.g = self.field(self.f)
 
     def field(self, f):
+        """rho, phi and g = -grad phi of f (Sec. 2.2)."""
         rho = density(f, self.grid)
         phi = poisson(rho, self.grid, self.p.G, self.p.poisson_bc, self.ghat)
         g = force(phi, self.grid, self.p.poisson_bc)
         return rho, phi, g
 
     def dt(self) -> float:
+        """The fixed dt, or C min(dt_p, dt_v) from the current g (Sec. 2.4)."""
         if self.p.dt_fixed > 0:
             return self.p.dt_fixed
         return timestep(self.g, self.grid, self.p.courant)
 
     def kick(self, g, tau):
+        """T_vz T_vy T_vx(tau) with acceleration g (Sec. 2.1, outflow in v)."""
         for a in range(3):                                   # vx, vy, vz
             self.lost += sweep(self.f, 3 + a, g[a], tau, self.grid.dv[a], False)
 
     def drift(self, tau):
+        """T_x T_y T_z(tau) with the cell-centre velocities (Sec. 2.1)."""
         per = self.p.space_bc == "periodic"
         for a in (2, 1, 0):                                  # z, y, x
             self.lost += sweep(self.f, a, self.grid.vc(a), tau, self.grid.dx[a], per)
@@ -358,11 +380,14 @@ class Simulation:
 
 
 def velocity_square(grid: Grid) -> np.ndarray:
+    """|v|^2 at the velocity cell centres (the K of Sec. 3.1)."""
     vx, vy, vz = (grid.vc(a) for a in range(3))
     return (vx[:, None, None] ** 2 + vy[None, :, None] ** 2 + vz[None, None, :] ** 2).reshape(-1)
 
 
 def energy(f: np.ndarray, grid: Grid, p: Params, ghat=None):
+    """(M, K, U, E) of f: Sec. 3.1 Eqs. (total_mass), (kinetic_energy) with
+    cell-centre velocities, Sec. 3.2 U = 1/2 sum rho phi dV_x, E = K + U."""
     np_ = int(np.prod(grid.n))
     nv = int(np.prod(grid.nv))
     v2 = velocity_square(grid)
