@@ -19,7 +19,11 @@ from oracle import vp_oracle as O  # noqa: E402
 
 from test_saturating_form import saturating_update, shifted_update  # noqa: E402
 
-values = st.floats(min_value=0.0, max_value=1.0, allow_nan=False, allow_infinity=False)
+# no subnormal values: for a line whose maximum F/2 is subnormal the kernels'
+# reciprocal -1/F overflows in FP64 (such lines leave the saturating form's
+# agreement with the oracle; in FP32 they are flushed to zero)
+values = st.floats(min_value=0.0, max_value=1.0, allow_nan=False, allow_infinity=False,
+                   allow_subnormal=False)
 lines = hnp.arrays(np.float64, st.integers(3, 24), elements=values)
 shifts = st.floats(min_value=-6.0, max_value=6.0, allow_nan=False).filter(lambda a: abs(a) > 1e-6)
 
@@ -48,7 +52,7 @@ def test_positive_homogeneity(f, alpha, periodic, scale):
     np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-14 * scale * max(f.max(), 1e-300))
 
 
-@settings(max_examples=300, deadline=None)
+@settings(max_examples=400, deadline=None)
 @given(f=lines, alpha=shifts, periodic=st.booleans())
 def test_kernel_formulations_agree_with_the_oracle(f, alpha, periodic):
     ref = O.pfc_line(f, alpha, periodic)

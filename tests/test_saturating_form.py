@@ -27,7 +27,8 @@ from oracle import vp_oracle as O
 
 
 def sat(x):
-    return np.minimum(np.maximum(x, 0.0), 1.0)
+    # fmin/fmax as the kernels' saturation: NaN goes to 0
+    return np.fmin(np.fmax(x, 0.0), 1.0)
 
 
 def saturating_update(f, alpha, periodic):
