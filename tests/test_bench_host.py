@@ -34,7 +34,11 @@ def test_kernel_source_hash_is_stable():
 
 
 def test_peak_is_the_measured_hbm_copy_rate():
-    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if not os.path.exists(path):                # not measured yet: the fallback figure
+        assert bench.load_peaks() == (6800.0, "fallback")
+        return
+    with open(path) as fh:
         hbm = float(json.load(fh)["hbm_gbs"])
     assert bench.load_peaks() == (hbm, "measured")
 
