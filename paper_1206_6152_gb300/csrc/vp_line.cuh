@@ -242,4 +242,35 @@ __device__ __forceinline__ V update_line(V (&x)[N], const LineW<V> &w, bool neg)
     }
 }
 
+// FP64 line update in the saturating form for any line maximum.  For a line
+// whose maximum lies below 2^-968 (subnormal or barely normal) the reciprocal
+// -1/F and the weights A1, A2 would overflow or lose their significant bits;
+// such a line is swept scaled by 2^968 and scaled back.  The PFC update is
+// positively homogeneous of degree one (scaling the line scales every face
+// flux), and a power of two scales without rounding, so the scaled sweep is
+// the same update; only the final scaling back rounds, into the subnormal
+// range, as the store of the unscaled result would.
+template <int N, bool PERIODIC>
+__device__ __forceinline__ double update_line_f64(double (&x)[N], double c0, double c1, double c2,
+                                                  int neg)
+{
+    constexpr double UP = 0x1p+968, DOWN = 0x1p-968;
+    double finf = line_max(x);
+    const bool tiny = finf > 0.0 && finf < DOWN;
+    if (tiny) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) x[j] *= UP;
+        finf *= UP;
+    }
+    LineW<double> w;
+    weights1<double>(c0, c1, c2, neg, finf, w.K0, w.A1, w.A2, w.ninvF);
+    double lost = update_line<double, N, PERIODIC>(x, w, neg);
+    if (tiny) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) x[j] *= DOWN;
+        lost *= DOWN;
+    }
+    return lost;
+}
+
 }  // namespace vpline

@@ -638,8 +638,7 @@ __global__ void __launch_bounds__(128, N <= 32 ? 4 : 1) k_drift_fast(const T *__
         } else {
             const int via = (int)((v / g.va_stride) % g.va_n);
             const LineCoef<T> ca = coef[via];
-            const LineW<V> w = weights_one<T>(ca, line_max(x));
-            lost += update_line<V, N, PERIODIC>(x, w, ca.code & 1);
+            lost += update_line_f64<N, PERIODIC>(x, ca.c0, ca.c1, ca.c2, ca.code & 1);
         }
         T *q = ob + v;
 #pragma unroll

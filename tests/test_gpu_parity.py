@@ -88,6 +88,41 @@ def test_each_sweep_matches_oracle(shape, dtype, space_bc):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("space_bc", ["periodic", "outflow"])
+def test_fp64_lines_with_subnormal_maximum(space_bc):
+    """FP64 position sweeps (the register kernels, lines of 16) of an f whose
+    lines have maxima in the subnormal range, next to lines of ordinary
+    size: every line matches the oracle to its own rounding (the kernels
+    rescale such a line by a power of two instead of letting -1/F
+    overflow)."""
+    w = I.small_maxwell(n=(16, 16, 16), nv=(2, 4, 6), dtype="f64", space_bc=space_bc)
+    grid = O.Grid.of(w)
+    rng = np.random.default_rng(17)
+    f0 = rng.random(w.shape) + 0.05
+    # velocity cells with tiny lines: scales from subnormal to barely normal
+    scales = [1e-310, 2.0 ** -1000, 7 * 5e-324, 1e-300, 1.0]
+    for k, s in enumerate(scales):
+        f0[..., k % 2, k % 4, k % 6] *= s
+    sim, f = gpu_sim(w, f0)
+    per = space_bc == "periodic"
+    for axis in range(3):
+        for tau in (0.011, -0.017):
+            f.copy_(torch.from_numpy(f0))
+            sim.sweep(axis, tau)
+            got = f.cpu().numpy()
+            ref = f0.copy()
+            O.sweep(ref, axis, grid.vc(axis), tau, grid.dx[axis], per)
+            for k, s in enumerate(scales):
+                sl = (Ellipsis, k % 2, k % 4, k % 6)
+                a, b = got[sl], ref[sl]
+                assert np.all(np.isfinite(a)) and a.min() >= 0.0
+                atol = 1e-12 * f0[sl].max() + 64 * 5e-324
+                assert np.abs(a - b).max() <= atol, (axis, tau, s, np.abs(a - b).max())
+            assert np.abs(got - ref).max() <= 1e-12 * f0.max()
+    sim.close()
+
+
+@pytest.mark.gpu
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_integer_courant_drift_is_exact(dtype):
     w = I.small_maxwell(n=(6, 5, 4), nv=(4, 6, 2), dtype=dtype, G=0.0)

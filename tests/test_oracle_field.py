@@ -105,3 +105,27 @@ def test_density_sums_velocity_cells():
     rho = O.density(f, g)
     dv = g.dvol_v
     assert np.array_equal(rho, f.reshape(12, -1).sum(1).reshape(g.n) * dv)
+
+
+def test_kinetic_energy_and_mass_closed_form():
+    """M and K (Sec. 3.1: M = sum f dV, K = 1/2 sum f |v|^2 dV with the
+    cell-centre velocity) of a hand-built f, worked out by hand.
+
+    Grid: 2 x 1 x 1 unit cells (dV_x = 1); velocity cells vx in [-3, 3) (3
+    cells: centres -2, 0, 2), vy in [-1, 3) (2 cells: centres 0, 2), vz in
+    [1, 2) (1 cell: centre 1.5), so dV_v = 2 * 2 * 1 = 4.  f = (x + 1)(i + 1)
+    with x the position index and i the vx index, the same for both vy.
+    Per x weight (x + 1): 1 + 2 = 3.  Sum over velocities of
+    (i + 1)|v|^2: i = 0 (vx^2 = 4): (4 + 0 + 2.25) + (4 + 4 + 2.25) = 16.5;
+    i = 1 (vx = 0): 2 * (2.25 + 6.25) = 17; i = 2: 3 * 16.5 = 49.5; total
+    83.  K = 1/2 * 4 * 3 * 83 = 498.  M = 4 * 3 * (1 + 2 + 3) * 2 = 144."""
+    grid = O.Grid((2, 1, 1), (3, 2, 1), (0.0, 0.0, 0.0), (2.0, 1.0, 1.0), (-3.0, -1.0, 1.0),
+                  (3.0, 3.0, 2.0))
+    f = np.zeros((2, 1, 1, 3, 2, 1))
+    for x in range(2):
+        for i in range(3):
+            f[x, 0, 0, i, :, 0] = (x + 1) * (i + 1)
+    M, K, U, E = O.energy(f, grid, O.Params(G=0.0))
+    assert M == 144.0
+    assert K == 498.0
+    assert U == 0.0 and E == K

@@ -19,11 +19,9 @@ from oracle import vp_oracle as O  # noqa: E402
 
 from test_saturating_form import saturating_update, shifted_update  # noqa: E402
 
-# no subnormal values: for a line whose maximum F/2 is subnormal the kernels'
-# reciprocal -1/F overflows in FP64 (such lines leave the saturating form's
-# agreement with the oracle; in FP32 they are flushed to zero)
-values = st.floats(min_value=0.0, max_value=1.0, allow_nan=False, allow_infinity=False,
-                   allow_subnormal=False)
+# subnormal values included: the FP64 kernels sweep a line whose maximum is
+# below 2^-968 rescaled by a power of two (restated in saturating_update)
+values = st.floats(min_value=0.0, max_value=1.0, allow_nan=False, allow_infinity=False)
 lines = hnp.arrays(np.float64, st.integers(3, 24), elements=values)
 shifts = st.floats(min_value=-6.0, max_value=6.0, allow_nan=False).filter(lambda a: abs(a) > 1e-6)
 

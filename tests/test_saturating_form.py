@@ -34,9 +34,15 @@ def sat(x):
 def saturating_update(f, alpha, periodic):
     if alpha < 0:
         return saturating_update(f[::-1].copy(), -alpha, periodic)[::-1]
+    # a line whose maximum is below 2^-968 is swept scaled by 2^968 (exact:
+    # the update is positively homogeneous) and scaled back, as the FP64
+    # kernels do, so that -1/F and the weights stay finite and normal
+    fmax = max(f.max(), 0.0)
+    if 0.0 < fmax < 2.0 ** -968:
+        return saturating_update(f * 2.0 ** 968, alpha, periodic) * 2.0 ** -968
     b = alpha
     c0, c1, c2 = b, b * (1 - b) * (2 - b) / 6, b * (1 - b) * (1 + b) / 6
-    F = 2.0 * max(f.max(), 0.0)
+    F = 2.0 * fmax
     ninvF = -1.0 / F if F > 0 else 0.0
     h = f * ninvF
     r3 = -3.0 * ninvF
@@ -127,6 +133,24 @@ def shifted_update(f, alpha, periodic):
     out = np.array([cell(i - s) - phi(i - s) + phi(i - s - 1) for i in range(n)])
     lost = 0.0 if periodic else sum(f[max(n - s, 0):]) + (phi(n - 1 - s) if n - 1 - s >= 0 else 0.0)
     return out, lost
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+@pytest.mark.parametrize("alpha", [0.3, 0.81, -0.47])
+@pytest.mark.parametrize("scale", [1e-310, 2.0 ** -1000, 5e-324 * 7, 1e-300])
+def test_subnormal_line_maximum(periodic, alpha, scale):
+    """Lines whose maximum is subnormal or barely normal: the rescaled
+    saturating form gives the oracle's update to the line's own rounding
+    (no reciprocal overflow, no loss of the corrector)."""
+    rng = np.random.default_rng(int(1e3 * abs(alpha)) + periodic)
+    for f in lines(rng, 19):
+        g = f * scale
+        got = saturating_update(g, alpha, periodic)
+        ref = O.pfc_line(g, alpha, periodic)
+        assert np.all(np.isfinite(got)) and got.min() >= 0.0
+        # subnormal arithmetic rounds to multiples of 2^-1074 in both forms
+        atol = 2e-15 * max(g.max(), 0.0) + 64 * 5e-324
+        np.testing.assert_allclose(got, ref, rtol=0, atol=atol)
 
 
 @pytest.mark.parametrize("periodic", [True, False])
