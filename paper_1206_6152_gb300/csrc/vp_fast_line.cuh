@@ -1,4 +1,4 @@
-// vp_fast_line.cuh -- FP32 line helpers of the register kernels, shared by
+// vp_fast_line.cuh -- line helpers of the register kernels, shared by
 // the forward sweeps (vp_sweep_fast.cu) and by the adjoint kernels that
 // recompute a forward sweep (vp_adjoint_fast.cu), so that a recomputed
 // sweep input is bitwise the one the forward pass produced.
@@ -6,6 +6,7 @@
 
 #include <cuda_runtime.h>
 
+#include "vp_device.cuh"
 #include "vp_internal.cuh"
 #include "vp_line.cuh"
 
@@ -59,5 +60,53 @@ __device__ __forceinline__ float drift_pair(float2 (&x)[N], const LineCoef<float
     for (int j = 0; j < N; ++j) x[j] = make_float2(y0[j], y1[j]);
     return lost;
 }
+
+__device__ __forceinline__ int upos(int j, int n, int neg) { return neg ? n - 1 - j : j; }
+
+// generic in-place line update in shared memory (any whole-cell shift,
+// outflow boundaries); used only for cube-sweeps with |alpha| >= 1
+template <typename T>
+__device__ __noinline__ T kick_line_shifted(T *L, int st, int n, const LineCoef<T> cf)
+{
+    const int s = cf.code >> 1, neg = cf.code & 1;
+    const T c0 = cf.c0, c1 = cf.c1, c2 = cf.c2;
+    T finf = T(0);
+    for (int j = 0; j < n; ++j) finf = fmax(finf, L[j * st]);
+    T lost = T(0);
+    for (int j = (n - s > 0 ? n - s : 0); j < n; ++j) lost += L[upos(j, n, neg) * st];
+    const int jtop = n - 1 - s;
+    if (jtop < 0) {
+        for (int i = 0; i < n; ++i) L[i * st] = T(0);
+        return lost;
+    }
+    auto fget = [&](int j) -> T { return (j >= 0 && j < n) ? L[upos(j, n, neg) * st] : T(0); };
+    T f0 = fget(jtop), fm = fget(jtop - 1);
+    T ph = pfc_flux(fm, f0, fget(jtop + 1), finf, c0, c1, c2);
+    lost += ph;
+    for (int i = n - 1; i >= 0; --i) {
+        const int j = i - s;
+        if (j < 0) {
+            L[upos(i, n, neg) * st] = T(0);
+            continue;
+        }
+        const T fmm = fget(j - 2);
+        const T phm = (j >= 1) ? pfc_flux(fmm, fm, f0, finf, c0, c1, c2) : T(0);
+        L[upos(i, n, neg) * st] = (f0 - ph) + phm;
+        f0 = fm;
+        fm = fmm;
+        ph = phm;
+    }
+    return lost;
+}
+
+// one sweep of the owned lines held in registers
+template <int N>
+__device__ __forceinline__ float sweep_pairs(float2 (&x)[N], const LineCoef<float> &cf)
+{
+    const LineW<float2> w = weights_pair(cf, line_max(x));
+    const float2 out = update_line<float2, N, false>(x, w, cf.code & 1);
+    return out.x + out.y;
+}
+
 
 }  // namespace vpline

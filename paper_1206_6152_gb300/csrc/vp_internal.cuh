@@ -133,11 +133,14 @@ int vp_kick_fast_ok(const vp_ctx *c);
 int vp_drift_fast_ok(const vp_ctx *c, int axis);
 int vp_rho_fuse_ok(const vp_ctx *c);
 int vp_rho_parts(vp_ctx *c);
-// FP32 cubes of edge 48: kick sweeps one pass per vx sweep and per run of
-// consecutive vy / vz sweeps, lines in registers
+// FP32 cubes of edge 48: whole half kicks and the fused kick in passes of
+// two sweeps on slabs (vp_kick_big.cu); other sweep runs one pass per vx
+// sweep and per run of consecutive vy / vz sweeps, lines in registers
 int vp_kick_big_ok(const vp_ctx *c);
 cudaError_t launch_kick_big(vp_ctx *c, void *f, const void *ca, const void *cb, int nsweeps,
                             int first_axis, void *fo = nullptr);
+cudaError_t launch_kick_big3(vp_ctx *c, float *f, const LineCoef<float> *ca,
+                             const LineCoef<float> *cb, int nsweeps, int first_axis, float *fo);
 // fused z then y drift of the whole grid (FP32, N_y = N_z in {16, 32}; in
 // place when fo == f)
 int vp_drift_yz_ok(const vp_ctx *c);

@@ -32,44 +32,6 @@ int vp_sm_count();
 
 namespace {
 
-__device__ __forceinline__ int upos(int j, int n, int neg) { return neg ? n - 1 - j : j; }
-
-// generic in-place line update in shared memory (any whole-cell shift,
-// outflow boundaries); used only for cube-sweeps with |alpha| >= 1
-template <typename T>
-__device__ __noinline__ T kick_line_shifted(T *L, int st, int n, const LineCoef<T> cf)
-{
-    const int s = cf.code >> 1, neg = cf.code & 1;
-    const T c0 = cf.c0, c1 = cf.c1, c2 = cf.c2;
-    T finf = T(0);
-    for (int j = 0; j < n; ++j) finf = fmax(finf, L[j * st]);
-    T lost = T(0);
-    for (int j = (n - s > 0 ? n - s : 0); j < n; ++j) lost += L[upos(j, n, neg) * st];
-    const int jtop = n - 1 - s;
-    if (jtop < 0) {
-        for (int i = 0; i < n; ++i) L[i * st] = T(0);
-        return lost;
-    }
-    auto fget = [&](int j) -> T { return (j >= 0 && j < n) ? L[upos(j, n, neg) * st] : T(0); };
-    T f0 = fget(jtop), fm = fget(jtop - 1);
-    T ph = pfc_flux(fm, f0, fget(jtop + 1), finf, c0, c1, c2);
-    lost += ph;
-    for (int i = n - 1; i >= 0; --i) {
-        const int j = i - s;
-        if (j < 0) {
-            L[upos(i, n, neg) * st] = T(0);
-            continue;
-        }
-        const T fmm = fget(j - 2);
-        const T phm = (j >= 1) ? pfc_flux(fmm, fm, f0, finf, c0, c1, c2) : T(0);
-        L[upos(i, n, neg) * st] = (f0 - ph) + phm;
-        f0 = fm;
-        fm = fmm;
-        ph = phm;
-    }
-    return lost;
-}
-
 // ---------------------------------------------------------------------------
 // kick: FP32 velocity cubes of edge N (16 or 32)
 //
@@ -195,16 +157,6 @@ __device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
 {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
-
-// one sweep of the owned lines held in registers
-template <int N>
-__device__ __forceinline__ float sweep_pairs(float2 (&x)[N], const LineCoef<float> &cf)
-{
-    const LineW<float2> w = weights_pair(cf, line_max(x));
-    const float2 out = update_line<float2, N, false>(x, w, cf.code & 1);
-    return out.x + out.y;
-}
-
 
 // whole cube through shared memory (a sweep moves by whole cells)
 template <int N>
@@ -1018,7 +970,9 @@ cudaError_t launch_kick_big(vp_ctx *c, void *f_, const void *ca_, const void *cb
     float *f = (float *)f_;
     float *fo = fo_ ? (float *)fo_ : f;   // the first pass reads f, every pass writes fo
     const LineCoef<float> *ca = (const LineCoef<float> *)ca_, *cb = (const LineCoef<float> *)cb_;
-    cudaError_t e;
+    // whole half kicks and the fused kick: passes of two sweeps on slabs
+    cudaError_t e = launch_kick_big3(c, f, ca, cb, nsweeps, first_axis, fo);
+    if (e != cudaErrorNotSupported) return e;
     for (int sw = 0; sw < nsweeps;) {
         const int va = (first_axis + sw) % 3;
         const LineCoef<float> *cf = sw < 3 ? ca : cb;

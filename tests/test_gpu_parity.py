@@ -477,6 +477,37 @@ def test_split_steps_48_cubes_match_oracle():
 
 
 @pytest.mark.gpu
+def test_split_steps_48_cubes_with_whole_cell_kicks():
+    """Fixed dt chosen so that the kick moves some cubes' lines by more than
+    one cell (|alpha| up to about 1.6) while others stay below one: both the
+    slab passes and their line-by-line fallback run in the same launches
+    (three-sweep prologue and tail, six-sweep body)."""
+    w = I.small_maxwell(n=(4, 4, 4), nv=(48, 48, 48), dtype="f32", amp=0.3, G=25.0)
+    w = w.replace(box_lo=(-0.5,) * 3, box_hi=(0.5,) * 3)
+    f0 = I.initial_condition(w)
+    grid = O.Grid.of(w)
+    g0 = O.force(O.poisson(O.density(f0.astype(np.float64), grid), grid, w.G, "periodic"),
+                 grid, "periodic")
+    amax = max(np.abs(g0[a]).max() / grid.dv[a] for a in range(3))
+    dt = 2 * 1.6 / amax                                    # half kick: |alpha| <= 1.6
+    alpha = np.max([np.abs(g0[a]) * dt / 2 / grid.dv[a] for a in range(3)], axis=0)
+    assert (alpha >= 1).sum() >= 4 and (alpha < 1).sum() >= 4
+    w = w.replace(dt_fixed=dt)
+    sim, f = gpu_sim(w, f0)
+    t = sim.step(2, sync=True)
+    got = f.cpu().numpy().astype(np.float64)
+    e = sim.energy()
+    ref = O.Simulation(f0.astype(np.float64), grid, O.Params.of(w))
+    ref.step(2)
+    r = ref.energy()
+    assert t == pytest.approx(2 * dt, rel=1e-14)
+    assert rel_l1(got, ref.f) <= 4e-6
+    assert got.min() >= 0.0
+    assert e["M_out"] == pytest.approx(r[4], rel=1e-4, abs=1e-7 * r[0])
+    sim.close()
+
+
+@pytest.mark.gpu
 @pytest.mark.slow
 def test_jeans48_full_size_sweeps_and_steps():
     """The 48^3 x 48^3 FP32 box (49 GB of f) in the benchmark's launch
