@@ -143,9 +143,12 @@ int vp_step_host(vp_ctx *ctx, const void *f_host_in, void *f_host_out, int nstep
  * and [2] brackets no kernel),
  *   [4] density reduction                      [5] Poisson + force
  *   [6] dt, shift tables, time                 [7] whole step
+ *   [8], [9], [10] the three passes of the fused kick of 48^3 velocity
+ *   cubes (vx+vy, vz+vx, vy+vz; [0] is their sum); 0 for other cubes, whose
+ *   fused kick is one pass.
  * The first and last half kicks around the timed body run untimed, so f
  * advances by two split steps, exactly as vp_step(ctx, 2).  Synchronises. */
-#define VP_PROFILE_SLOTS 8
+#define VP_PROFILE_SLOTS 11
 int vp_profile_step(vp_ctx *ctx, double *ms_out);
 
 /* Number of kernels vp_step has launched on the device since vp_init

@@ -23,8 +23,9 @@ EXPORTS = (
     "vp_profile_step", "vp_stats", "vp_sweep_adjoint", "vp_moments_noalloc",
     "vp_set_adjoint_states", "vp_check", "vp_debug_fail_alloc",
 )
-PROFILE_SLOTS = 8
-PROFILE_NAMES = ("kick6", "drift_z", "drift_y", "drift_x", "density", "field", "tables", "step")
+PROFILE_SLOTS = 11
+PROFILE_NAMES = ("kick6", "drift_z", "drift_y", "drift_x", "density", "field", "tables", "step",
+                 "kick_a", "kick_b", "kick_c")
 
 
 class VPError(RuntimeError):

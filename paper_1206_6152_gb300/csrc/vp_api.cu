@@ -629,6 +629,8 @@ int vp_profile_step(vp_ctx *c, double *ms_out)
     if (!c || !ms_out) return VP_ERR_ARG;
     cudaEvent_t ev[12];
     for (int i = 0; i < 12; ++i) VP_CUDA_TRY(cudaEventCreate(&ev[i]));
+    for (int i = 8; i < 11; ++i) ms_out[i] = 0.0;
+    const bool big_kick = vp_kick_big_ok(c) != 0;      // the fused kick runs as three passes
     int r = VP_OK;
     auto rec = [&](int i) { return cudaEventRecord(ev[i], c->stream); };
 #define PROF(x)                                                              \
@@ -670,7 +672,12 @@ int vp_profile_step(vp_ctx *c, double *ms_out)
     PROF(launch_coef_kick(c, c->g, &c->sc->dt, 0.5, c->coef_kick1));
     PROF(launch_coef_drift(c, &c->sc->dt, 1.0, c->coef_drift));
     PROF(rec(6));
-    PROF(launch_kick(c, c->f, c->coef_kick2, c->coef_kick1, 6, 0));
+    if (big_kick) c->kick_pass_ev = ev + 8;
+    {
+        const cudaError_t ek = launch_kick(c, c->f, c->coef_kick2, c->coef_kick1, 6, 0);
+        c->kick_pass_ev = nullptr;
+        PROF(ek);
+    }
     PROF(rec(7));
     // close the step: drift, field and the final half kick, untimed
     if ((r = enqueue_body(c, 1)) != VP_OK) goto done;
@@ -684,6 +691,11 @@ int vp_profile_step(vp_ctx *c, double *ms_out)
         }
         PROF(cudaEventElapsedTime(&ms, ev[0], ev[7]));
         ms_out[7] = ms;
+        if (big_kick)
+            for (int i = 0; i < 3; ++i) {
+                PROF(cudaEventElapsedTime(&ms, ev[8 + i], ev[9 + i]));
+                ms_out[8 + i] = ms;
+            }
     }
 #undef PROF
 done:

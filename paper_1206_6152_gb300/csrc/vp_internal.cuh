@@ -98,6 +98,10 @@ struct vp_ctx {
                                 // reads; some may share a buffer), or two to recompute into
     int adj_nstates;
     int adj_mode;               // 0 automatic, 1 two states, 2 the kept sweep inputs
+
+    // tracing: when set, the kick of 48^3 cubes records an event before
+    // its first pass and after each pass (vp_profile_step)
+    cudaEvent_t *kick_pass_ev;
 };
 
 // ---------------------------------------------------------------------------

@@ -390,17 +390,23 @@ cudaError_t launch_kick_big3(vp_ctx *c, float *f, const LineCoef<float> *ca,
     unsigned grid;
     const size_t smem_a = (size_t)B::A_TILE * sizeof(float);
     const size_t smem_bc = (size_t)B::BC_TILE * sizeof(float);
+    cudaEvent_t *ev = c->kick_pass_ev;
+    if (ev && (e = cudaEventRecord(ev[0], c->stream)) != cudaSuccess) return e;
     if ((e = persistent_grid(k_kick_pass_a<N>, B::NT, smem_a, nunits, grid)) != cudaSuccess) return e;
     k_kick_pass_a<N><<<grid, B::NT, smem_a, c->stream>>>(f, ca, nunits, &c->sc->lost, fo);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[1], c->stream)) != cudaSuccess) return e;
     if (nsweeps == 6) {
         if ((e = persistent_grid(k_kick_pass_b<N>, B::NT, smem_bc, nunits, grid)) != cudaSuccess) return e;
         k_kick_pass_b<N><<<grid, B::NT, smem_bc, c->stream>>>(fo, ca, cb, nunits, &c->sc->lost, fo);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    if (ev && (e = cudaEventRecord(ev[2], c->stream)) != cudaSuccess) return e;
     const LineCoef<float> *cc = nsweeps == 6 ? cb : ca;
     if ((e = persistent_grid(k_kick_pass_c<N>, B::NT, smem_bc, nunits, grid)) != cudaSuccess) return e;
     k_kick_pass_c<N><<<grid, B::NT, smem_bc, c->stream>>>(fo, cc, nsweeps == 6 ? 1 : 0, nunits,
                                                            &c->sc->lost, fo);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[3], c->stream)) != cudaSuccess) return e;
+    return cudaSuccess;
 }

@@ -18,13 +18,38 @@ from paper_1206_6152_gb300 import inputs as I  # noqa: E402
 def test_traffic_is_reported_only_for_the_sources_it_was_measured_on(monkeypatch):
     with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
         t = json.load(fh)
-    for kernel in ("kick6", "drift_yz", "drift_x"):
-        ent = t[kernel]
+    assert t, "no traffic entries"
+    for key, ent in t.items():
         monkeypatch.setattr(bench, "kernel_source_hash", lambda h=ent["source_hash"]: h)
-        assert bench.load_traffic(kernel) == pytest.approx(ent["dram_bytes_per_launch_full"])
+        assert bench.load_traffic(key) == pytest.approx(ent["dram_bytes_per_launch_full"])
         monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
-        assert bench.load_traffic(kernel) is None
+        assert bench.load_traffic(key) is None
     assert bench.load_traffic("no_such_kernel") is None
+
+
+def test_traffic_is_recorded_from_an_ncu_launch_list(tmp_path, monkeypatch):
+    """An ncu --csv launch list of one 48^6 step: each pass's DRAM bytes per
+    launch, the two drift launches of one kernel told apart by their order."""
+    rows = ['"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"']
+    names = ["k_drift_fast<float, 48, 1, 0>(...)", "k_drift_fast<float, 48, 1, 0>(...)",
+             "k_drift_fast<float, 48, 1, 1>(...)", "k_kick_pass_a<48>(...)",
+             "k_kick_pass_b<48>(...)", "k_kick_pass_c<48>(...)"]
+    for i, n in enumerate(names):
+        rows.append(f'"{i}","{n}","dram__bytes_read.sum","Gbyte","{10 + i}"')
+        rows.append(f'"{i}","{n}","dram__bytes_write.sum","Mbyte","{500 + i}"')
+        rows.append(f'"{i}","{n}","gpu__time_duration.sum","msecond","{2 + i}"')
+    csv_path = tmp_path / "l.csv"
+    csv_path.write_text("\n".join(rows) + "\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "ab" * 8)
+    out = bench.record_traffic(str(csv_path), "w48")
+    want = {"drift_z": 0, "drift_y": 1, "drift_x": 2, "kick_a": 3, "kick_b": 4, "kick_c": 5}
+    for slot, i in want.items():
+        e = out[f"w48:{slot}"]
+        assert e["dram_bytes_per_launch_full"] == pytest.approx((10 + i) * 1e9 + (500 + i) * 1e6)
+        assert e["duration_us_under_ncu"] == pytest.approx((2 + i) * 1e3)
+        assert e["source_hash"] == "ab" * 8
 
 
 def test_kernel_source_hash_is_stable():
@@ -46,8 +71,8 @@ def test_peak_is_the_measured_hbm_copy_rate():
 def test_oracle_step_rate_scales_its_samples():
     w = I.small_maxwell(n=(8, 4, 4), nv=(8, 8, 8), dtype="f64", amp=0.2)
     f0 = I.initial_condition(w)
-    rate, full, desc = bench.oracle_step_rate(w, f0, 0.25)
-    assert rate > 0 and full > 0
+    rate, full, desc, measured = bench.oracle_step_rate(w, f0, 0.25)
+    assert rate > 0 and full > 0 and measured > 0
     assert rate == pytest.approx(w.cells / full)
     # 2 of 8 x planes of velocity cubes and 2 of 8 vx columns of velocity cells
     assert "(0.2500)" in desc and desc.count("(0.2500)") == 2
@@ -68,8 +93,20 @@ def test_reference_steps_sample_the_density():
     f0 = I.initial_condition(w)
     rho = bench.oracle_density(w, f0)
     assert rho.shape == tuple(w.n)
-    rate, full, desc = bench.oracle_step_rate(w, f0, 0.25, rho)
+    rate, full, desc, _ = bench.oracle_step_rate(w, f0, 0.25, rho)
     assert rate > 0 and "density timed on 2 of 8 x planes" in desc
+
+
+def test_samples_from_the_factors_equal_the_initial_condition():
+    """The oracle's samples of a separable initial condition are built from
+    its two factors without a host copy of f: the same values."""
+    import numpy as np
+    w = I.small_maxwell(n=(8, 4, 4), nv=(8, 6, 4), dtype="f64", amp=0.2)
+    f0 = I.initial_condition(w)
+    src = bench.HostSource(w)
+    assert np.array_equal(src.planes(2, 5), f0[2:5])
+    assert np.array_equal(src.vcols(3), f0[:, :, :, :3])
+    np.testing.assert_allclose(src.density(), bench.oracle_density(w, f0), rtol=1e-13)
 
 
 def test_cores_are_the_oracles_openmp_threads():
