@@ -233,9 +233,14 @@ int vp_functional(vp_ctx *ctx, int kind, const double *target, void *lambda_f,
  * Asynchronous on cuda_stream.  The per-cell partial sums live in one
  * static device array of the library sized for at most 262144 spatial cells
  * (64^3; 4 MiB, held on every GPU that loads the library until the process
- * exits); larger grids return VP_ERR_UNSUPPORTED.  The first call on each
+ * exits); larger grids return VP_ERR_UNSUPPORTED.  f_dev and sums_dev must
+ * be device memory of the current device, else VP_ERR_ARG (checked with
+ * cudaPointerGetAttributes before any launch).  The first call on each
  * device looks up that array's device address (cudaGetSymbolAddress) and
- * caches it, so make the first call on a device before any stream capture.
+ * caches it with the id of the current CUDA context, so make the first call
+ * on a device before any stream capture; after a device reset the next
+ * call, made in the new context, looks the address up again (make it, too,
+ * outside a capture).
  * Every call writes all the partials it reads, so no state carries over
  * between calls, but all calls share the one array: calls that overlap on
  * the GPU (different streams, or a stream and a graph) race and must be

@@ -327,10 +327,14 @@ class Simulation:
     Eq. (integration), read right to left: half kick vx, vy, vz with g^n,
     drift z, y, x, field of the drifted f, half kick with g^{n+1}."""
 
-    def __init__(self, f: np.ndarray, grid: Grid, params: Params):
+    def __init__(self, f: np.ndarray, grid: Grid, params: Params, copy: bool = True):
+        """copy=False adopts f itself when it is a contiguous FP64 array (a
+        69 GB state would otherwise be held twice); the steps then update it
+        in place."""
         self.grid = grid
         self.p = params
-        self.f = np.ascontiguousarray(f, dtype=np.float64).copy()
+        c = np.ascontiguousarray(f, dtype=np.float64)
+        self.f = c.copy() if (copy and c is f) else c
         self.t = 0.0
         self.lost = 0.0                  # phase-space sum that left (unscaled)
         self.ghat = None

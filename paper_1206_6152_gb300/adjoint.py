@@ -37,6 +37,15 @@ def _free_bytes(dev: torch.device) -> int:
     return free
 
 
+def _release_pinned() -> None:
+    """Returns the page-locked host memory torch keeps cached after pinned
+    tensors are freed (checkpoints of a 49 GB state fill half the host's
+    memory) to the system."""
+    fn = getattr(torch._C, "_host_emptyCache", None)
+    if fn is not None:
+        fn()
+
+
 def _store(t: torch.Tensor, on_device: bool) -> torch.Tensor:
     if on_device:
         return t.clone()
@@ -59,10 +68,11 @@ class _Trajectory(torch.autograd.Function):
             f.copy_(f0)
             sim.refresh_field()
             ckpts: List[Tuple[torch.Tensor, torch.Tensor]] = []
-            for n in range(nsteps):
-                if n % every == 0:
-                    ckpts.append((_store(f, ck_dev), sim.field()[2]))
-                sim.step(1)
+            # one call per segment: between two checkpoints the steps run as
+            # the fused body (K2^n and K1^{n+1} in one pass over f)
+            for n0 in range(0, nsteps, every):
+                ckpts.append((_store(f, ck_dev), sim.field()[2]))
+                sim.step(min(every, nsteps - n0))
             lam_f = torch.empty_like(f)
             J = sim.functional(kind, lam_f, target)
         ctx.sim, ctx.nsteps, ctx.every = sim, nsteps, every
@@ -89,6 +99,9 @@ class _Trajectory(torch.autograd.Function):
                     # states of the segment: f^n, g^n for n0 <= n < n1
                     f.copy_(fc)
                     sim.set_accel(gc)
+                    # every step-start state is kept, so the steps run one
+                    # call each (inside a fused body the state between two
+                    # steps is never in memory)
                     states = []
                     for n in range(n0, n1):
                         states.append((f.clone(), sim.field()[2]))
@@ -108,8 +121,15 @@ class _Trajectory(torch.autograd.Function):
                         sim.adjoint_step(f, sim.field()[2], lam_f, lam_g)
             # g^0 = -grad phi[rho(f^0)]
             sim.field_adjoint(lam_g, lam_f)
-        grad = lam_f * gJ.to(lam_f.dtype)
-        return grad, None, None, None, None, None, None
+            on_host = any(not fc.is_cuda for fc, _ in ctx.ckpts)
+            ctx.ckpts = None
+            if on_host:
+                _release_pinned()
+            # the cotangent itself becomes the gradient (no second array of
+            # f's size: at 48^6 that would not fit beside the adjoint's scratch)
+            lam_f.mul_(gJ.to(lam_f.dtype))
+        ctx.lam_f = None
+        return lam_f, None, None, None, None, None, None
 
 
 def trajectory_functional(f0: torch.Tensor, sim: VlasovPoisson, nsteps: int, every: int = 10,

@@ -62,20 +62,28 @@ namespace {
 //   = kf f_j + Fd1 s1 + Fd2 s2,  kf = 1 + 2 (c1' - c2'), Fd1 = -F c1', Fd2 = F c2'
 template <typename V>
 struct AdjW {
-    V K0, c3a, c3b, nc1, c2, kf, Fd1, Fd2;
+    V nK0, c3a, c3b, nc1, c2, kf, Fd1, Fd2;    // nK0 = -K0
     V ninvF, r3;
 };
 
-__device__ __forceinline__ float nsel1(bool p) { return p ? -1.f : 0.f; }
+// an arm with saturation s of its argument u: interior iff s == u.  Returns
+// nm = -mu [interior] and g = [saturated at 1] (s when not interior, which
+// is 0 when saturated at 0), both selected by the one comparison
+__device__ __forceinline__ void arm1(float s, float u, float nmu, float &nm, float &g)
+{
+    const bool in = s == u;
+    nm = in ? nmu : 0.f;
+    g = in ? 0.f : s;
+}
 
 template <typename V>
 struct AOps;
 template <>
 struct AOps<float2> {
-    // -[a == b]
-    __device__ __forceinline__ static float2 neq(float2 a, float2 b)
+    __device__ __forceinline__ static void arm(float2 s, float2 u, float2 nmu, float2 &nm, float2 &g)
     {
-        return make_float2(nsel1(a.x == b.x), nsel1(a.y == b.y));
+        arm1(s.x, u.x, nmu.x, nm.x, g.x);
+        arm1(s.y, u.y, nmu.y, nm.y, g.y);
     }
     __device__ __forceinline__ static float2 fsat(float2 a, float2 b, float2 c)
     {
@@ -84,16 +92,20 @@ struct AOps<float2> {
 };
 template <>
 struct AOps<float> {
-    __device__ __forceinline__ static float neq(float a, float b) { return nsel1(a == b); }
+    __device__ __forceinline__ static void arm(float s, float u, float nmu, float &nm, float &g)
+    {
+        arm1(s, u, nmu, nm, g);
+    }
     __device__ __forceinline__ static float fsat(float a, float b, float c) { return fmasat(a, b, c); }
 };
 
-__device__ __forceinline__ void adj_weights1(const LineCoef<float> &cf, float finf, float &K0,
+__device__ __forceinline__ void adj_weights1(const LineCoef<float> &cf, float finf, float &nK0,
                                              float &c3a, float &c3b, float &nc1, float &c2,
                                              float &kf, float &Fd1, float &Fd2, float &ninvF)
 {
     float A1, A2;
-    weights1<float>(cf.c0, cf.c1, cf.c2, cf.code & 1, finf, K0, A1, A2, ninvF);
+    weights1<float>(cf.c0, cf.c1, cf.c2, cf.code & 1, finf, nK0, A1, A2, ninvF);
+    nK0 = -nK0;
     const float beta = cf.c0;
     c3a = 3.f * cf.c1;
     c3b = -3.f * cf.c2;
@@ -111,9 +123,9 @@ __device__ __forceinline__ AdjW<float2> adj_weights(const LineCoef<float> &ca,
                                                     const LineCoef<float> &cb, float2 finf)
 {
     AdjW<float2> w;
-    adj_weights1(ca, finf.x, w.K0.x, w.c3a.x, w.c3b.x, w.nc1.x, w.c2.x, w.kf.x, w.Fd1.x, w.Fd2.x,
+    adj_weights1(ca, finf.x, w.nK0.x, w.c3a.x, w.c3b.x, w.nc1.x, w.c2.x, w.kf.x, w.Fd1.x, w.Fd2.x,
                  w.ninvF.x);
-    adj_weights1(cb, finf.y, w.K0.y, w.c3a.y, w.c3b.y, w.nc1.y, w.c2.y, w.kf.y, w.Fd1.y, w.Fd2.y,
+    adj_weights1(cb, finf.y, w.nK0.y, w.c3a.y, w.c3b.y, w.nc1.y, w.c2.y, w.kf.y, w.Fd1.y, w.Fd2.y,
                  w.ninvF.y);
     w.r3 = __fmul2_rn(w.ninvF, make_float2(-3.f, -3.f));
     return w;
@@ -122,7 +134,7 @@ __device__ __forceinline__ AdjW<float2> adj_weights(const LineCoef<float> &ca,
 __device__ __forceinline__ AdjW<float> adj_weights(const LineCoef<float> &cf, float finf)
 {
     AdjW<float> w;
-    adj_weights1(cf, finf, w.K0, w.c3a, w.c3b, w.nc1, w.c2, w.kf, w.Fd1, w.Fd2, w.ninvF);
+    adj_weights1(cf, finf, w.nK0, w.c3a, w.c3b, w.nc1, w.c2, w.kf, w.Fd1, w.Fd2, w.ninvF);
     w.r3 = w.ninvF * -3.f;
     return w;
 }
@@ -130,16 +142,18 @@ __device__ __forceinline__ AdjW<float> adj_weights(const LineCoef<float> &cf, fl
 // One cell of the line adjoint (upwind position j).  In: the cell f0, the
 // scaled neighbours hprev, hnext, the output cotangents lo = l_j, ln =
 // l_{j+1}, the pending input cotangent pend of cell j - 1 and nm1p =
-// -m1_{j-1}.  With mu = ln - lo, nI = -[arm interior] and nm = mu nI:
+// -m1_{j-1}.  With mu = ln - lo and nm = -mu [arm interior]:
 //   l^in_{j-1} = pend - c2 m2_j                         (returned in done)
 //   pend'      = lo + K0 mu - 3 c1 m1_j + 3 c2 m2_j + c1 m1_{j-1}
-// and the line sums G1 += mu g1, G2 += mu g2 with g = s + nI u, which is
-// exactly the indicator of the arm saturated at 1 (0 when interior, s when
-// saturated), so that l_F = c2 G2 - c1 G1.  DB: S1, S2, SF accumulate
-// mu s1, mu s2 and mu f.
+// and the line sums of mu g1, mu g2 with g = [arm saturated at 1] (each term
+// exact: no cancellation), so that l_F = c2 sum mu g2 - c1 sum mu g1.  DB:
+// the sums of mu s1, mu s2 and mu f as well.  The sums are kept negated (they
+// accumulate -mu, which the arms' selection gives for free); finish() turns
+// them back, bitwise as the positive sums would be (an FMA rounds
+// symmetrically).
 template <typename V, bool DB>
 struct AdjCell {
-    V pend, nm1p, G1, G2, S1, S2, SF;
+    V pend, nm1p, G1, G2, S1, S2, SF;      // G, S: negated sums
 
     __device__ __forceinline__ void init()
     {
@@ -152,27 +166,27 @@ struct AdjCell {
     {
         typedef VOps<V> O;
         typedef AOps<V> A;
-        const V mu = O::sub(ln, lo);
+        const V nmu = O::sub(lo, ln);
         const V u1 = O::fma(f0, w.r3, hnext);
         const V u2 = O::fma(f0, w.r3, hprev);
         const V s1 = A::fsat(f0, w.r3, hnext);
         const V s2 = A::fsat(f0, w.r3, hprev);
-        const V nI1 = A::neq(s1, u1), nI2 = A::neq(s2, u2);
-        const V nm1 = O::mul(mu, nI1);
-        nm2 = O::mul(mu, nI2);
-        V x = O::fma(w.K0, mu, lo);
+        V nm1, g1, g2;
+        A::arm(s1, u1, nmu, nm1, g1);
+        A::arm(s2, u2, nmu, nm2, g2);
+        V x = O::fma(w.nK0, nmu, lo);
         x = O::fma(w.c3a, nm1, x);
         x = O::fma(w.c3b, nm2, x);
         if (!FIRST) x = O::fma(w.nc1, nm1p, x);
         const V done = O::fma(w.c2, nm2, pend);
         pend = x;
         nm1p = nm1;
-        G1 = O::fma(mu, O::fma(nI1, u1, s1), G1);
-        G2 = O::fma(mu, O::fma(nI2, u2, s2), G2);
+        G1 = O::fma(nmu, g1, G1);
+        G2 = O::fma(nmu, g2, G2);
         if (DB) {
-            S1 = O::fma(mu, s1, S1);
-            S2 = O::fma(mu, s2, S2);
-            SF = O::fma(mu, f0, SF);
+            S1 = O::fma(nmu, s1, S1);
+            S2 = O::fma(nmu, s2, S2);
+            SF = O::fma(nmu, f0, SF);
         }
         return done;
     }
@@ -180,8 +194,9 @@ struct AdjCell {
     __device__ __forceinline__ void finish(const AdjW<V> &w, V &lF, V &db) const
     {
         typedef VOps<V> O;
-        lF = O::fma(w.c2, G2, O::mul(w.nc1, G1));
-        db = DB ? O::fma(w.Fd2, S2, O::fma(w.Fd1, S1, O::mul(w.kf, SF))) : O::zero();
+        const V m1 = O::splat(typename O::S(-1));
+        lF = O::mul(O::fma(w.c2, G2, O::mul(w.nc1, G1)), m1);
+        db = DB ? O::mul(O::fma(w.Fd2, S2, O::fma(w.Fd1, S1, O::mul(w.kf, SF))), m1) : O::zero();
     }
 };
 

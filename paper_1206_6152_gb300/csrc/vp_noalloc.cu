@@ -16,7 +16,14 @@
 // the process exits.  Host code may not take the array's address directly
 // (its name on the host is only a stand-in for the device symbol), so the
 // first call on each device asks the runtime for the device address with
-// cudaGetSymbolAddress and caches it for that device.
+// cudaGetSymbolAddress and caches it for that device, together with the
+// unique id of the CUDA context it was looked up in: a call made in another
+// context (after a device reset, the runtime creates a new one) looks the
+// address up again.  Before any launch the input and output pointers are
+// checked to be device memory of the current device (a host pointer would
+// fault or read the wrong memory).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <mutex>
 
@@ -86,19 +93,44 @@ __global__ void k_moment_finish(const double *__restrict__ partials, long long n
 
 std::mutex g_setup_lock;
 double *g_scratch_addr[VP_NOALLOC_MAX_DEVICES];
+unsigned long long g_scratch_ctx[VP_NOALLOC_MAX_DEVICES];     // context id of the lookup
 
-// device address of g_moment_scratch on the current device (set up once per
-// device; the device must be current)
-int scratch_for_current_device(double **out)
+// unique id of the current CUDA context (0 if the driver cannot say: the
+// address is then looked up on every call)
+unsigned long long current_context_id()
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
+    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static bool resolved = false;
+    if (!resolved) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(p);
         cudaGetLastError();
-        return VP_ERR_CUDA;
+        resolved = true;
     }
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// device address of g_moment_scratch in the current context (set up on the
+// first call on each device and again whenever the device's context has
+// changed; the device must be current)
+int scratch_for_current_device(int dev, double **out)
+{
     if (dev < 0 || dev >= VP_NOALLOC_MAX_DEVICES) return VP_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lk(g_setup_lock);
-    if (!g_scratch_addr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_moment_scratch);
         if (e != cudaSuccess || !p) {
@@ -106,9 +138,22 @@ int scratch_for_current_device(double **out)
             return VP_ERR_CUDA;
         }
         g_scratch_addr[dev] = (double *)p;
+        g_scratch_ctx[dev] = ctx;
     }
     *out = g_scratch_addr[dev];
     return VP_OK;
+}
+
+// true if p is device (or managed) memory the current device can address as
+// its own
+bool on_device(const void *p, int dev)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 }  // namespace
@@ -126,11 +171,15 @@ extern "C" int vp_moments_noalloc(const void *f_dev, int dtype, const int n[3], 
     }
     const long long nvc = (long long)nv[0] * nv[1] * nv[2];
     if (np > VP_NOALLOC_MAX_CELLS || nvc > 0x7fffffffLL) return VP_ERR_UNSUPPORTED;
-    double *scratch = nullptr;
-    const int r = scratch_for_current_device(&scratch);
-    if (r != VP_OK) return r;
     int dev = 0;
-    cudaGetDevice(&dev);
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return VP_ERR_CUDA;
+    }
+    if (!on_device(f_dev, dev) || !on_device(sums_dev, dev)) return VP_ERR_ARG;
+    double *scratch = nullptr;
+    const int r = scratch_for_current_device(dev, &scratch);
+    if (r != VP_OK) return r;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     long long grid = (long long)sm_count_of(dev) * 8;
     if (grid > np) grid = np;

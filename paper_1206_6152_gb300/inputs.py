@@ -418,10 +418,11 @@ def king_profile(w0: float = 6.0) -> KingProfile:
     return KingProfile(w0=w0, r=r, W=W, r_t=r_t, rho0=rho0, rho1=rho1, sigma_c=sigma_c)
 
 
-def king_initial_condition(w: Workload, dtype) -> np.ndarray:
-    """King DF at the cell centres, before the virial renormalisation; for
-    ic "king2" the sum of two King spheres centred at x = -+ king_sep / 2 and
-    moving at v_x = +- king_u (towards each other)."""
+def king_factors(w: Workload):
+    """The pieces of the King DF at the cell centres: per sphere the relative
+    potential Psi on the spatial centres (flat) and |v - u|^2 on the velocity
+    centres (flat), and the normalisation; f = norm sum_spheres
+    expm1(Psi - |v - u|^2 / 2) where that is positive (sigma = 1)."""
     prof = king_profile(w.king_w0)
     xs = [w.centres_x(a) for a in range(3)]
     vx, vy, vz = (w.centres_v(a) for a in range(3))
@@ -437,6 +438,35 @@ def king_initial_condition(w: Workload, dtype) -> np.ndarray:
         psis.append(prof.psi(r).reshape(-1))             # sigma = 1
         v2s.append(((vx - ux)[:, None, None] ** 2 + vy[None, :, None] ** 2
                     + vz[None, None, :] ** 2).reshape(-1))
+    return psis, v2s, norm
+
+
+def king_initial_condition_device(w: Workload, device, dtype):
+    """king_initial_condition() evaluated in FP64 on a torch device from the
+    same factors (rounded once to dtype; expm1 is the device's, so a value
+    can differ from the host evaluation in its last FP64 bit)."""
+    import torch
+    psis, v2s, norm = king_factors(w)
+    npos, nvel = psis[0].size, v2s[0].size
+    out = torch.empty((npos, nvel), dtype=dtype, device=device)
+    ps = [torch.from_numpy(p).to(device) for p in psis]
+    vs = [torch.from_numpy(v).to(device) for v in v2s]
+    step = max(1, (1 << 26) // nvel)
+    for s in range(0, npos, step):
+        e = min(npos, s + step)
+        acc = torch.zeros((e - s, nvel), dtype=torch.float64, device=device)
+        for p, v in zip(ps, vs):
+            E = p[s:e, None] - 0.5 * v[None, :]
+            acc += torch.where(E > 0, torch.expm1(torch.clamp(E, min=0.0)), torch.zeros_like(E))
+        out[s:e] = (norm * acc).to(dtype)
+    return out.reshape(w.shape)
+
+
+def king_initial_condition(w: Workload, dtype) -> np.ndarray:
+    """King DF at the cell centres, before the virial renormalisation; for
+    ic "king2" the sum of two King spheres centred at x = -+ king_sep / 2 and
+    moving at v_x = +- king_u (towards each other)."""
+    psis, v2s, norm = king_factors(w)
     npos, nvel = psis[0].size, v2s[0].size
     out = np.empty((npos, nvel), dtype=dtype)
     step = max(1, (1 << 24) // nvel)

@@ -281,3 +281,76 @@ def test_jeans32_modes3_gradient_fp32_matches_fd():
           - _J_of(sim, _mode_f0(w, amps0 * (1 - eps), torch.float32), nsteps, 0, None)) / (2 * eps)
     assert float(np.dot(grad, amps0.cpu().numpy())) == pytest.approx(fd, rel=1e-3)
     sim.close()
+
+
+def _fill_mode_f0(w, amps, out):
+    """out <- f0(A) = rho_bar (1 + sum_m A_m cos(k_m.x + th_m)) M(v) in FP64,
+    rounded once to out's dtype, in chunks of positions (a 49 GB f has no
+    room for an FP64 copy)."""
+    fields = torch.from_numpy(I.mode_fields(w).reshape(len(w.modes), -1)).to(DEV)
+    rho = w.rho_bar * (1 + torch.as_tensor(list(amps), dtype=torch.float64, device=DEV) @ fields)
+    mv = torch.from_numpy(I.maxwellian_v(w).reshape(-1)).to(DEV)
+    o = out.view(rho.numel(), -1)
+    step = max(1, (1 << 26) // mv.numel())
+    for s in range(0, rho.numel(), step):
+        o[s:s + step] = (rho[s:s + step, None] * mv[None, :]).to(out.dtype)
+    return out
+
+
+@pytest.mark.gpu
+@pytest.mark.slow
+def test_jeans48_modes8_trajectory_gradient_matches_fd():
+    """The 48^3 x 48^3 FP32 forward+adjoint workload at a reduced step count:
+    20 steps from f0(A) with checkpoints every 10 (two checkpoints; they go
+    to pinned host memory because the device cannot hold them beside f, the
+    cotangent and the adjoint's two scratch states) and every step-start
+    state recomputed from its checkpoint.  The gradient of the final field
+    energy with respect to the eight mode amplitudes, dJ/dA_m = rho_bar
+    sum_x cos(k_m.x + th_m) sum_v lambda_0(x, v) M(v) with lambda_0 = dJ/df0
+    per cell, against central differences (1% of each amplitude; J is
+    quadratic in A in the linear regime), errors against the largest
+    component, and along the amplitude vector itself."""
+    from paper_1206_6152_gb300.adjoint import trajectory_functional
+    from paper_1206_6152_gb300.vlasov import VlasovPoisson, config_of
+    w = I.large_c5()
+    nsteps, every = 20, 10
+    amps0 = np.array([m[1] for m in w.modes])
+    f = torch.zeros(w.shape, dtype=torch.float32, device=DEV)
+    sim = VlasovPoisson(config_of(w), f)
+    f0 = _fill_mode_f0(w, amps0, torch.empty_like(f)).requires_grad_(True)
+    J = trajectory_functional(f0, sim, nsteps, every=every, kind=0, keep_states=False)
+    J.backward()
+    lam0 = f0.grad
+    mv = torch.from_numpy(I.maxwellian_v(w).reshape(-1)).to(DEV)
+    npos = int(np.prod(w.n))
+    s = torch.empty(npos, dtype=torch.float64, device=DEV)
+    lv = lam0.view(npos, -1)
+    for a in range(0, npos, 2304):
+        s[a:a + 2304] = lv[a:a + 2304].double() @ mv
+    fields = torch.from_numpy(I.mode_fields(w).reshape(len(w.modes), -1)).to(DEV)
+    grad = (w.rho_bar * (fields @ s)).cpu().numpy()
+    del f0, lam0, lv, J
+    torch.cuda.empty_cache()
+
+    lam = torch.empty_like(f)
+
+    def J_of(amps):
+        with torch.no_grad():
+            _fill_mode_f0(w, amps, sim.f)
+            sim.refresh_field()
+            sim.step(nsteps)
+            return sim.functional(0, lam)
+
+    fds = []
+    for m in range(len(amps0)):
+        h = 0.01 * amps0[m]
+        ap, am = amps0.copy(), amps0.copy()
+        ap[m] += h
+        am[m] -= h
+        fds.append((J_of(ap) - J_of(am)) / (2 * h))
+    fds = np.array(fds)
+    assert np.abs(grad - fds).max() <= 1e-3 * np.abs(fds).max(), (grad, fds)
+    eps = 0.01
+    fd = (J_of(amps0 * (1 + eps)) - J_of(amps0 * (1 - eps))) / (2 * eps)
+    assert float(np.dot(grad, amps0)) == pytest.approx(fd, rel=1e-3)
+    sim.close()

@@ -128,3 +128,65 @@ def test_king_merger_accounting_and_approach():
     assert abs(cm0) <= 1e-6 * w.dx[0] and abs(cm) <= 1e-3 * w.dx[0]
     assert sep <= sep0 - 4 * w.dx[0]
     sim.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.slow
+def test_king64x32_full_size_two_steps_match_oracle():
+    """The 64^3 x 32^3 FP32 King W0 = 6 workload (isolated Poisson on the
+    doubled 128^3 grid, outflow in position and velocity, adaptive dt) at
+    full size against the FP64 oracle, element by element, over two steps.
+    The initial condition is the King DF with its analytic normalisation,
+    built on the device; the oracle starts from the same FP32 values."""
+    from paper_1206_6152_gb300.vlasov import VlasovPoisson, config_of
+    w = I.king_c3()
+    f = I.king_initial_condition_device(w, DEV, torch.float32)       # 34 GB
+    f0 = f.cpu().numpy()
+    sim = VlasovPoisson(config_of(w, torch.float32), f)
+    M0 = sim.energy()["M"]
+    t = sim.step(2, sync=True)
+    e = sim.energy()
+    ref = O.Simulation(f0, O.Grid.of(w), O.Params.of(w))            # 69 GB FP64
+    del f0
+    got = f.cpu().numpy()
+    sim.close()
+    del f
+    torch.cuda.empty_cache()
+    ref.step(2)
+    assert abs(t - ref.t) <= 1e-6 * ref.t
+    num = den = 0.0
+    for i in range(w.n[0]):
+        d = np.abs(got[i].astype(np.float64) - ref.f[i])
+        num += d.sum()
+        den += np.abs(ref.f[i]).sum()
+    assert num / den <= 1e-5, num / den
+    assert got.min() >= 0.0
+    r = ref.energy()
+    assert abs(e["M"] + e["M_out"] - M0) <= 1e-7 * M0
+    assert e["M_out"] == pytest.approx(r[4], rel=1e-4, abs=1e-9 * M0)
+    assert e["M"] == pytest.approx(r[0], rel=1e-7)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-11), (torch.float32, 1e-5)])
+def test_small_king_merger_matches_oracle(dtype, tol):
+    """The merger set-up of Sec. 3.6 (two W0 = 3 King spheres approaching
+    each other at 0.5 sigma_c, velocity bounds 3 sigma_c + u, so the
+    velocity grid is asymmetric about each sphere's bulk motion; isolated
+    Poisson, outflow in position and velocity) on a 16 x 8 x 8 x 16^3 grid
+    through the whole split step, against the FP64 oracle."""
+    w = I.king_merger(nv=16).replace(n=(16, 8, 8))
+    f0 = I.initial_condition(w, np.float64)
+    grid = O.Grid.of(w)
+    osim = O.Simulation(f0, grid, O.Params.of(w))
+    sim, f = gpu_sim(w, f0.astype(np.float32) if dtype == torch.float32 else f0, dtype)
+    t = sim.step(3, sync=True)
+    osim.step(3)
+    got = f.cpu().numpy().astype(np.float64)
+    assert abs(t - osim.t) <= (1e-13 if dtype == torch.float64 else 1e-6) * osim.t
+    assert np.abs(got - osim.f).sum() / np.abs(osim.f).sum() <= tol
+    assert got.min() >= 0.0
+    e1, r1 = sim.energy(), osim.energy()
+    assert e1["M_out"] == pytest.approx(r1[4], rel=1e-4, abs=1e-12 * r1[0])
+    assert e1["E"] == pytest.approx(r1[3], rel=1e-5)
+    sim.close()
