@@ -217,6 +217,55 @@ int vp_field_adjoint(vp_ctx *ctx, const double *lambda_g, void *lambda_f);
 int vp_functional(vp_ctx *ctx, int kind, const double *target, void *lambda_f,
                   double *J_out);
 
+/* ---------------------------------------------------------------------
+ * Position space cut into slabs along x, one slab per GPU (the
+ * decomposition of Sec. 2.3: position space divided among the processes,
+ * velocity space kept whole).  A slab's context is made by vp_init with the
+ * slab's own grid (n[0] = its planes, box_lo[0]/box_hi[0] its extent, the
+ * same cell widths).  Kicks and the y and z drifts are slab-local
+ * (vp_sweep); the x drift needs the neighbours' planes and the maximum of
+ * every whole x line (vp_line_max_x, vp_drift_x_ghosted); the field is
+ * solved from the gathered density by a field-only context of the whole
+ * grid (vp_field_init, vp_field_solve) on every GPU, and the slab's part of
+ * g is handed to the slab's context (vp_set_accel).  The exchanges between
+ * GPUs are the caller's (paper_1206_6152_gb300/sharded.py: all-reduce of the
+ * line maxima, halo planes, all-gather of the density).  Periodic position
+ * space only.
+ * ------------------------------------------------------------------- */
+
+/* Per-line maxima along x of the context's f: lmax_dev[(y, z, v)] = max(0,
+ * max_i f[i][y][z][v]) over the slab's planes, laid out [ny][nz][nvx][nvy]
+ * [nvz] in f's dtype (device, ny nz nvx nvy nvz elements, caller-owned).
+ * The maximum of a whole line (f_inf of Sec. 2.1) is the maximum of these
+ * over the slabs.  Asynchronous.  VP_ERR_STATE for a field-only context. */
+int vp_line_max_x(vp_ctx *ctx, void *lmax_dev);
+
+/* The x drift T_x(tau) (Sec. 2.1, Eq. (adv_xpos)) of the context's slab,
+ * in place, for x lines that continue beyond it: ghost_lo holds the nghost
+ * planes below the slab (the lower neighbour's last planes; in periodic
+ * space the last planes of the whole box for the first slab), ghost_hi the
+ * nghost planes above it, each laid out [nghost][ny][nz][nvx][nvy][nvz] in
+ * f's dtype (device, caller-owned, read only); lmax_dev the maxima of the
+ * whole lines (vp_line_max_x reduced over the slabs).  The update of a cell
+ * reads up to floor(|alpha|) + 2 cells upwind and one downwind, so nghost
+ * must be at least floor(max |v_x| tau / dx) + 2; else VP_ERR_ARG.
+ * Asynchronous. */
+int vp_drift_x_ghosted(vp_ctx *ctx, double tau, const void *ghost_lo, const void *ghost_hi,
+                       int nghost, const void *lmax_dev);
+
+/* A context for the field alone (Sec. 2.2: Poisson and force on the
+ * config's grid, periodic or isolated), with no distribution function:
+ * vp_field_solve, vp_get_field and vp_destroy only (the calls that need f
+ * return VP_ERR_STATE).  Errors as vp_init. */
+int vp_field_init(const vp_config *cfg, void *cuda_stream, vp_ctx **out);
+
+/* phi and g = -grad phi of the density rho_dev (device, N_x N_y N_z
+ * doubles) on the context's grid; g is copied to g_dev (device, 3 N_x N_y
+ * N_z doubles, [axis][x][y][z]) unless NULL.  With dt_out (host), also the
+ * timestep of Sec. 2.4 for that g (the fixed dt if configured); that
+ * synchronises.  VP_ERR_NONFINITE for a non-finite dt. */
+int vp_field_solve(vp_ctx *ctx, const double *rho_dev, double *g_dev, double *dt_out);
+
 /* Allocation-free moments (the paper has no counterpart; this is a service
  * for callers that cannot allocate device memory when they need the
  * diagnostic -- e.g. code inside a CUDA stream capture, which an allocation

@@ -131,19 +131,25 @@ static double face_flux(const double *f, long n, long i, long s, double beta,
 /* Forward PFC update of one line with alpha >= 0 (Sec. 2.1, Eq. (conserve)
  * as f_i + Phi^- - Phi^+, the line maximum taken at t^n); a rounding-negative
  * result is set to 0. */
-static void pfc_line_pos(const double *f, double *out, long n, double alpha,
-                         int periodic)
+static void pfc_line_pos_max(const double *f, double *out, long n, double alpha,
+                             int periodic, double finf)
 {
     long s = (long)floor(alpha);
     double beta = alpha - (double)s;
-    double finf = 0.0;
-    for (long j = 0; j < n; ++j) if (f[j] > finf) finf = f[j];
     for (long i = 0; i < n; ++i) {
         double phi_minus = face_flux(f, n, i - 1, s, beta, finf, periodic);
         double phi_plus = face_flux(f, n, i, s, beta, finf, periodic);
         double v = f[i] + phi_minus - phi_plus;
         out[i] = v > 0.0 ? v : 0.0;
     }
+}
+
+static void pfc_line_pos(const double *f, double *out, long n, double alpha,
+                         int periodic)
+{
+    double finf = 0.0;
+    for (long j = 0; j < n; ++j) if (f[j] > finf) finf = f[j];
+    pfc_line_pos_max(f, out, n, alpha, periodic, finf);
 }
 
 /* Public: one line, any sign of alpha (u < 0 as the mirror image of u > 0,
@@ -160,6 +166,29 @@ void oracle_pfc_line(const double *fin, double *fout, long n, double alpha,
         for (long j = 0; j < n; ++j) a[j] = fin[n - 1 - j];
         pfc_line_pos(a, b, n, -alpha, periodic);
         for (long j = 0; j < n; ++j) fout[j] = b[n - 1 - j];
+    }
+}
+
+/* Public: the update of the n cells of a piece of a longer line (the
+ * decomposition of position space into slabs, Sec. 2.3).  ext holds the
+ * piece with G cells of the line on each side (ext[G + j] = cell j,
+ * j in [-G, n + G)), finf is the maximum of the whole line.  A cell's update
+ * reads cells i - s - 2 .. i + 1 (u >= 0; mirrored for u < 0) and finf only,
+ * so with G >= floor(|alpha|) + 2 it is, bit for bit, the one
+ * oracle_pfc_line computes on the whole line. */
+void oracle_pfc_line_ghosted(const double *ext, double *out, long n, long G, double alpha,
+                             double finf)
+{
+    const long m = n + 2 * G;
+    double a[m], b[m];
+    if (alpha >= 0.0) {
+        memcpy(a, ext, sizeof(double) * (size_t)m);
+        pfc_line_pos_max(a, b, m, alpha, 0, finf);
+        memcpy(out, b + G, sizeof(double) * (size_t)n);
+    } else {
+        for (long j = 0; j < m; ++j) a[j] = ext[m - 1 - j];
+        pfc_line_pos_max(a, b, m, -alpha, 0, finf);
+        for (long j = 0; j < n; ++j) out[j] = b[m - 1 - (G + j)];
     }
 }
 
@@ -369,6 +398,34 @@ double oracle_sweep(double *f, const long dims[6], int axis,
         if (!periodic) lost += before - after;
     }
     return lost;
+}
+
+/* The x sweep of a slab of nx = dims[0] position planes (Sec. 2.3's
+ * decomposition): every x line continues into G planes below (glo) and
+ * above (ghi) the slab, each laid out as [G][ny][nz][nv...], and has the
+ * maximum lmax[(y, z, v)] over the whole line.  out receives the slab's
+ * updated planes.  speed: the dims[3] cell-centre velocities along x. */
+void oracle_sweep_x_ghosted(const double *f, const double *glo, const double *ghi,
+                            double *out, const long dims[6], long G, const double *speed,
+                            double tau, double h, const double *lmax)
+{
+    const long nx = dims[0];
+    long nl = 1;
+    for (int a = 1; a < 6; ++a) nl *= dims[a];
+    const long nvc = dims[3] * dims[4] * dims[5];
+#pragma omp parallel for schedule(static)
+    for (long l = 0; l < nl; ++l) {
+        double ext[nx + 2 * G], res[nx];
+        for (long j = 0; j < G; ++j) {
+            ext[j] = glo[j * nl + l];
+            ext[G + nx + j] = ghi[j * nl + l];
+        }
+        for (long i = 0; i < nx; ++i) ext[G + i] = f[i * nl + l];
+        const long vx = (l % nvc) / (dims[4] * dims[5]);
+        const double alpha = speed[vx] * tau / h;
+        oracle_pfc_line_ghosted(ext, res, nx, G, alpha, lmax[l]);
+        for (long i = 0; i < nx; ++i) out[i * nl + l] = res[i];
+    }
 }
 
 /* Adjoint of oracle_sweep at input fin (not in the paper; frozen arms).

@@ -85,6 +85,12 @@ def lib():
             L.oracle_sweep_adjoint.argtypes = [dp, dp, lp, ctypes.c_int, dp, ctypes.c_double,
                                                ctypes.c_double, ctypes.c_int, dp]
             L.oracle_sweep_adjoint.restype = None
+            L.oracle_pfc_line_ghosted.argtypes = [dp, dp, ctypes.c_long, ctypes.c_long,
+                                                  ctypes.c_double, ctypes.c_double]
+            L.oracle_pfc_line_ghosted.restype = None
+            L.oracle_sweep_x_ghosted.argtypes = [dp, dp, dp, dp, lp, ctypes.c_long, dp,
+                                                 ctypes.c_double, ctypes.c_double, dp]
+            L.oracle_sweep_x_ghosted.restype = None
             L.oracle_density.argtypes = [dp, ctypes.c_long, ctypes.c_long, ctypes.c_double, dp]
             L.oracle_density.restype = None
             L.oracle_moments.argtypes = [dp, ctypes.c_long, ctypes.c_long, dp, dp]
@@ -142,6 +148,38 @@ def sweep(f: np.ndarray, axis: int, speed: np.ndarray, tau: float, h: float,
     sp = np.ascontiguousarray(speed, dtype=np.float64).reshape(-1)
     return lib().oracle_sweep(_dptr(f), _dims(f), int(axis), _dptr(sp), float(tau), float(h),
                               int(bool(periodic)))
+
+
+def pfc_line_ghosted(ext: np.ndarray, n: int, G: int, alpha: float, finf: float) -> np.ndarray:
+    """The update of the n cells ext[G:G+n] of a piece of a longer line whose
+    G neighbouring cells on each side are ext[:G] and ext[G+n:] and whose
+    maximum is finf (Sec. 2.1 on a line split across the slabs of Sec. 2.3);
+    with G >= floor(|alpha|) + 2 it equals the whole-line update there."""
+    e = np.ascontiguousarray(ext, dtype=np.float64)
+    assert e.size == n + 2 * G
+    out = np.empty(n)
+    lib().oracle_pfc_line_ghosted(_dptr(e), _dptr(out), n, G, float(alpha), float(finf))
+    return out
+
+
+def sweep_x_ghosted(f: np.ndarray, glo: np.ndarray, ghi: np.ndarray, speed: np.ndarray,
+                    tau: float, h: float, lmax: np.ndarray) -> np.ndarray:
+    """T_x(tau) of a slab of x planes f[nx][ny][nz][nvx][nvy][nvz] whose x
+    lines continue into the G planes glo below and ghi above it (periodic
+    wrap included by whoever filled them) and have the maxima lmax
+    [ny][nz][nvx][nvy][nvz] over the whole line (Sec. 2.3's decomposition of
+    position space).  Returns the slab's updated planes."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    glo = np.ascontiguousarray(glo, dtype=np.float64)
+    ghi = np.ascontiguousarray(ghi, dtype=np.float64)
+    lm = np.ascontiguousarray(lmax, dtype=np.float64)
+    G = glo.shape[0]
+    assert glo.shape == ghi.shape == (G,) + f.shape[1:] and lm.shape == f.shape[1:]
+    out = np.empty_like(f)
+    sp = np.ascontiguousarray(speed, dtype=np.float64).reshape(-1)
+    lib().oracle_sweep_x_ghosted(_dptr(f), _dptr(glo), _dptr(ghi), _dptr(out), _dims(f), G,
+                                 _dptr(sp), float(tau), float(h), _dptr(lm))
+    return out
 
 
 def sweep_adjoint(fin: np.ndarray, lam: np.ndarray, axis: int, speed: np.ndarray, tau: float,

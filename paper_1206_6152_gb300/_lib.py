@@ -21,7 +21,8 @@ EXPORTS = (
     "vp_moments", "vp_get_field", "vp_set_accel", "vp_energy", "vp_time", "vp_step_host",
     "vp_adjoint_step", "vp_field_adjoint", "vp_functional", "vp_destroy", "vp_error_string",
     "vp_profile_step", "vp_stats", "vp_sweep_adjoint", "vp_moments_noalloc",
-    "vp_set_adjoint_states", "vp_check", "vp_debug_fail_alloc",
+    "vp_set_adjoint_states", "vp_check", "vp_debug_fail_alloc", "vp_line_max_x",
+    "vp_drift_x_ghosted", "vp_field_init", "vp_field_solve",
 )
 PROFILE_SLOTS = 11
 PROFILE_NAMES = ("kick6", "drift_z", "drift_y", "drift_x", "density", "field", "tables", "step",
@@ -93,6 +94,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "vp_stats": (i, [vp, ctypes.POINTER(ctypes.c_longlong)]),
             "vp_check": (i, [vp, ctypes.POINTER(ctypes.c_longlong)]),
             "vp_debug_fail_alloc": (i, [i]),
+            "vp_line_max_x": (i, [vp, vp]),
+            "vp_drift_x_ghosted": (i, [vp, d, vp, vp, i, vp]),
+            "vp_field_init": (i, [ctypes.POINTER(vp_config), vp, ctypes.POINTER(vp)]),
+            "vp_field_solve": (i, [vp, vp, vp, dp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)

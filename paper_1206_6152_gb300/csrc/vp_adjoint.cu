@@ -794,6 +794,7 @@ int vp_field_adjoint(vp_ctx *c, const double *lambda_g, void *lambda_f)
 int vp_functional(vp_ctx *c, int kind, const double *target, void *lambda_f, double *J_out)
 {
     if (!c || !lambda_f || (kind != 0 && kind != 1) || (kind == 1 && !target)) return VP_ERR_ARG;
+    if (!c->f) return VP_ERR_STATE;
     const int T = 256;
     VP_CUDA_TRY(launch_density(c, c->f, c->rho2));
     double *sums = c->red + 2 * c->np;
@@ -912,6 +913,7 @@ int vp_adjoint_step(vp_ctx *c, const void *f_start, const double *g_start, void 
                     double *lambda_g)
 {
     if (!c || !f_start || !g_start || !lambda_f || !lambda_g) return VP_ERR_ARG;
+    if (!c->f) return VP_ERR_STATE;
     if (!(c->cfg.dt_fixed > 0.0)) return VP_ERR_STATE;
     TRY(ensure_adjoint_scratch(c));
     const double dt = c->cfg.dt_fixed;

@@ -351,9 +351,15 @@ const char *vp_error_string(int code)
     }
 }
 
-int vp_init(const vp_config *cfg, void *f_dev, void *cuda_stream, vp_ctx **out)
+}  // extern "C"
+
+namespace {
+
+// the context of vp_init; without f (f_dev == nullptr) only what the field
+// solve needs is used and no field is computed
+int init_ctx(const vp_config *cfg, void *f_dev, void *cuda_stream, vp_ctx **out)
 {
-    if (!cfg || !f_dev || !out) return VP_ERR_ARG;
+    if (!cfg || !out) return VP_ERR_ARG;
     *out = nullptr;
     TRY(check_config(cfg));
     vp_ctx *c = new (std::nothrow) vp_ctx();
@@ -445,16 +451,35 @@ int vp_init(const vp_config *cfg, void *f_dev, void *cuda_stream, vp_ctx **out)
     if ((r = build_twiddles(c))) return fail(r);
     if ((r = build_green(c))) return fail(r);
     k_zero_lost<<<1, 1, 0, c->stream>>>(c->sc, 0.0);
-    if ((r = field_from_f(c))) return fail(r);
+    if (c->f && (r = field_from_f(c))) return fail(r);
     e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) { vp_note_cuda_error(e, "vp_init sync", __FILE__, __LINE__); return fail(VP_ERR_CUDA); }
     *out = c;
     return VP_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int vp_init(const vp_config *cfg, void *f_dev, void *cuda_stream, vp_ctx **out)
+{
+    if (!f_dev) {
+        if (out) *out = nullptr;
+        return VP_ERR_ARG;
+    }
+    return init_ctx(cfg, f_dev, cuda_stream, out);
+}
+
+int vp_field_init(const vp_config *cfg, void *cuda_stream, vp_ctx **out)
+{
+    return init_ctx(cfg, nullptr, cuda_stream, out);
+}
+
 int vp_refresh_field(vp_ctx *c)
 {
     if (!c) return VP_ERR_ARG;
+    if (!c->f) return VP_ERR_STATE;
     return field_from_f(c);
 }
 
@@ -471,6 +496,7 @@ int vp_set_distribution(vp_ctx *c, void *f_dev)
 int vp_step(vp_ctx *c, int nsteps, double *t_out)
 {
     if (!c || nsteps < 0) return VP_ERR_ARG;
+    if (!c->f) return VP_ERR_STATE;
     if (nsteps > 0) {
         TRY(ensure_graphs(c));
         VP_CUDA_TRY(cudaGraphLaunch(c->g_first, c->stream));
@@ -491,6 +517,7 @@ int vp_step(vp_ctx *c, int nsteps, double *t_out)
 int vp_sweep(vp_ctx *c, int axis, double tau)
 {
     if (!c || axis < 0 || axis > 5 || !isfinite(tau)) return VP_ERR_ARG;
+    if (!c->f) return VP_ERR_STATE;
     double *tau_ptr = &c->sc->pad[0];
     k_set_scalar<<<1, 1, 0, c->stream>>>(tau_ptr, tau);
     VP_CUDA_TRY(cudaGetLastError());
@@ -508,6 +535,7 @@ int vp_sweep(vp_ctx *c, int axis, double tau)
 int vp_moments(vp_ctx *c, double *rho_dev)
 {
     if (!c || !rho_dev) return VP_ERR_ARG;
+    if (!c->f) return VP_ERR_STATE;
     VP_CUDA_TRY(launch_density(c, c->f, rho_dev));
     return VP_OK;
 }
@@ -536,6 +564,7 @@ int vp_set_accel(vp_ctx *c, const double *g_dev)
 int vp_energy(vp_ctx *c, double out[5])
 {
     if (!c || !out) return VP_ERR_ARG;
+    if (!c->f) return VP_ERR_STATE;
     // M and K: per-cell partials, then a compensated reduction
     VP_CUDA_TRY(launch_energy_partials(c, c->f, c->red));
     double *sums = c->red + 2 * c->np;
@@ -575,6 +604,7 @@ int vp_step_host(vp_ctx *c, const void *f_host_in, void *f_host_out, int nsteps,
                  double *diag_out)
 {
     if (!c || !f_host_in || nsteps < 0) return VP_ERR_ARG;
+    if (!c->f) return VP_ERR_STATE;
     const size_t bytes = (size_t)c->ncells * c->esize;
     VP_CUDA_TRY(cudaMemcpyAsync(c->f, f_host_in, bytes, cudaMemcpyHostToDevice, c->stream));
     TRY(field_from_f(c));
@@ -592,6 +622,7 @@ int vp_step_host(vp_ctx *c, const void *f_host_in, void *f_host_out, int nsteps,
 int vp_check(vp_ctx *c, long long *counts)
 {
     if (!c) return VP_ERR_ARG;
+    if (!c->f) return VP_ERR_STATE;
     unsigned long long *cnt = reinterpret_cast<unsigned long long *>(c->red);
     VP_CUDA_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), c->stream));
     const unsigned grid = (unsigned)(vp_sm_count() * 8);
@@ -627,6 +658,7 @@ int vp_stats(vp_ctx *c, long long *kernels_launched)
 int vp_profile_step(vp_ctx *c, double *ms_out)
 {
     if (!c || !ms_out) return VP_ERR_ARG;
+    if (!c->f) return VP_ERR_STATE;
     cudaEvent_t ev[12];
     for (int i = 0; i < 12; ++i) VP_CUDA_TRY(cudaEventCreate(&ev[i]));
     for (int i = 8; i < 11; ++i) ms_out[i] = 0.0;
