@@ -519,6 +519,35 @@ def test_split_steps_48_cubes_with_whole_cell_kicks():
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("whole_cell", [False, True])
+def test_split_steps_32_cubes(whole_cell):
+    """FP32 split steps with 32^3 velocity cubes (the fused kick pass of the
+    32^6 benchmark box) on 4^3 positions against the oracle; with
+    whole_cell, a fixed dt under which the kick moves half of the cubes by
+    more than one cell (those cubes take the in-place generic routine)."""
+    w = I.small_maxwell(n=(4, 4, 4), nv=(32, 32, 32), dtype="f32", amp=0.3, G=25.0)
+    w = w.replace(box_lo=(-0.5,) * 3, box_hi=(0.5,) * 3)
+    f0 = I.initial_condition(w)
+    grid = O.Grid.of(w)
+    if whole_cell:
+        g0 = O.force(O.poisson(O.density(f0.astype(np.float64), grid), grid, w.G, "periodic"),
+                     grid, "periodic")
+        amax = max(np.abs(g0[a]).max() / grid.dv[a] for a in range(3))
+        w = w.replace(dt_fixed=2 * 1.6 / amax)
+    sim, f = gpu_sim(w, f0)
+    t = sim.step(3, sync=True)
+    got = f.cpu().numpy().astype(np.float64)
+    e = sim.energy()
+    ref = O.Simulation(f0.astype(np.float64), grid, O.Params.of(w))
+    ref.step(3)
+    assert abs(t - ref.t) <= 1e-6 * ref.t
+    assert rel_l1(got, ref.f) <= 4e-6
+    assert got.min() >= 0.0
+    assert e["M_out"] == pytest.approx(ref.energy()[4], rel=1e-4, abs=1e-7 * ref.energy()[0])
+    sim.close()
+
+
+@pytest.mark.gpu
 @pytest.mark.slow
 def test_jeans48_full_size_sweeps_and_steps():
     """The 48^3 x 48^3 FP32 box (49 GB of f) in the benchmark's launch
