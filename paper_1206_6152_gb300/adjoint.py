@@ -84,6 +84,11 @@ class _Trajectory(torch.autograd.Function):
         sim: VlasovPoisson = ctx.sim
         f = sim.f
         fbytes = f.numel() * f.element_size()
+        if f.is_cuda:
+            # the adjoint's scratch states are allocated by the library, outside
+            # torch's caching allocator: blocks torch keeps cached would not be
+            # available to it
+            torch.cuda.empty_cache()
         with torch.no_grad():
             lam_f = ctx.lam_f
             lam_g = torch.zeros((3,) + tuple(sim.cfg.n), dtype=torch.float64, device=f.device)

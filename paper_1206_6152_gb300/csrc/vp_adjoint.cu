@@ -283,9 +283,25 @@ __global__ void __launch_bounds__(256) k_broadcast_box(T *__restrict__ lam_f,
                                                       long long np)
 {
     for (long long cell = blockIdx.x; cell < np; cell += gridDim.x) {
-        const double v = bc[cell];
         T *q = lam_f + cell * nvc;
-        for (long long e = threadIdx.x; e < nvc; e += blockDim.x) q[e] = (T)((double)q[e] + v);
+        if constexpr (sizeof(T) == 4) {
+            // FP32 cotangent: the cell's value rounded once to FP32 and added
+            // in FP32 (an FP64 add per element costs GB300 1/64 of the rate)
+            const float v = (float)bc[cell];
+            if ((nvc & 3) == 0) {
+                float4 *q4 = reinterpret_cast<float4 *>(q);
+                for (long long e = threadIdx.x; e < nvc / 4; e += blockDim.x) {
+                    float4 a = q4[e];
+                    a.x += v; a.y += v; a.z += v; a.w += v;
+                    q4[e] = a;
+                }
+            } else {
+                for (long long e = threadIdx.x; e < nvc; e += blockDim.x) q[e] += v;
+            }
+        } else {
+            const double v = bc[cell];
+            for (long long e = threadIdx.x; e < nvc; e += blockDim.x) q[e] = q[e] + v;
+        }
     }
 }
 

@@ -1,6 +1,6 @@
 // vp_adjoint_fast.cu -- FP32 register-line adjoint sweeps for line lengths
-// 16 and 32 (zero whole-cell shift): the transpose of the forward kernels of
-// vp_sweep_fast.cu with their own limiter arms.
+// 16, 32 and 48 (zero whole-cell shift): the transpose of the forward kernels
+// of vp_sweep_fast.cu with their own limiter arms.
 //
 // Forward (vp_line.cuh), in the upwind frame of a line with F = 2 f_inf,
 // h_j = -f_j / F and r3 = 3 / F:
@@ -368,7 +368,7 @@ struct PairGeom {
 // of thread t at j * 128 + t: conflict-free) and streamed from there, which
 // keeps the kernel at 128 registers (16 warps per SM).
 template <int N, bool PERIODIC, bool DB, bool BC, bool MIXED>
-__global__ void __launch_bounds__(128, 4) k_adjoint_pairs(const float *__restrict__ fin,
+__global__ void __launch_bounds__(128, N <= 32 ? 4 : 2) k_adjoint_pairs(const float *__restrict__ fin,
                                                       float *__restrict__ lam,
                                                       const LineCoef<float> *__restrict__ coef,
                                                       PairGeom g, const double *__restrict__ bc,
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(128, 4) k_adjoint_pairs(const float *__restric
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int t = threadIdx.x;
     float2 *sl = reinterpret_cast<float2 *>(smem_raw) + t;     // slot j: sl[j * 128]
-    long long base, u0, u1, stride, cell0 = 0;
+    long long base, u0, u1, stride, cell0 = 0, cube = 0;
     if (g.axis < 3) {
         const int o = blockIdx.y;
         cell0 = (long long)(o / g.od) * g.m1 + (long long)(o % g.od) * g.m2;
@@ -394,9 +394,12 @@ __global__ void __launch_bounds__(128, 4) k_adjoint_pairs(const float *__restric
             __syncthreads();
         }
     } else {
-        base = (long long)blockIdx.y * g.nvc;
+        // velocity axes: the cube on the grid's x dimension (any number of
+        // cubes), the chunk of its line pairs on y
+        cube = blockIdx.x;
+        base = cube * g.nvc;
         stride = g.vstride;
-        u0 = (long long)blockIdx.x * blockDim.x;
+        u0 = (long long)blockIdx.y * blockDim.x;
         u1 = u0 + blockDim.x;
         if (u1 > g.units) u1 = g.units;
     }
@@ -418,15 +421,27 @@ __global__ void __launch_bounds__(128, 4) k_adjoint_pairs(const float *__restric
             cb = coef[(int)(((v + 1) / g.va_stride) % g.va_n)];
         } else {
             off = base + (u / g.pd) * g.pm_hi + 2 * (u % g.pd);
-            ca = coef[blockIdx.y * 3 + (g.axis - 3)];
+            ca = coef[cube * 3 + (g.axis - 3)];
             cb = ca;
             if (g.cube3) {
-                const LineCoef<float> *cc = coef + blockIdx.y * 3;
+                const LineCoef<float> *cc = coef + cube * 3;
                 cb.code |= (cc[0].code | cc[1].code | cc[2].code) & ~1;
             }
         }
         if ((ca.code >> 1) != 0 || (cb.code >> 1) != 0) {
             atomicExch(skipped, 1);
+            if constexpr (BC) {
+                // the fix-up pass sweeps this pair: it gets its density
+                // broadcast here, as the pairs swept below do on load
+#pragma unroll 4
+                for (int j = 0; j < N; ++j) {
+                    float2 *p = reinterpret_cast<float2 *>(lam + off + j * stride);
+                    float2 v = *p;
+                    v.x += sbc[j];
+                    v.y += sbc[j];
+                    *p = v;
+                }
+            }
             continue;
         }
         // lines of one direction are read in upwind order (u < 0: from the
@@ -485,7 +500,7 @@ __global__ void __launch_bounds__(128, 4) k_adjoint_pairs(const float *__restric
     }
     if (DB) {
         const double s = block_sum((double)da, red);
-        if (t == 0 && s != 0.0) atomicAdd(lam_g + blockIdx.y, s * scale);
+        if (t == 0 && s != 0.0) atomicAdd(lam_g + cube, s * scale);
     }
 }
 
@@ -818,26 +833,38 @@ __global__ void __launch_bounds__(AdjYZ<N>::NT, 2) k_drift_adjoint_yz(
     }
 }
 
+// dynamic shared memory above the default 48 KB (static included) must be
+// allowed per kernel before its launch
+template <class K>
+cudaError_t allow_smem(K kernel, size_t dyn)
+{
+    if (dyn + 1024 <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+}
+
+template <int N, bool PERIODIC, bool DB, bool BC, bool MIXED>
+cudaError_t pairs_launch(vp_ctx *c, const float *fin, float *lam, const LineCoef<float> *coef,
+                         const PairGeom &g, dim3 grid, const double *bc, double *lam_g, double scale)
+{
+    constexpr size_t smem = (size_t)N * 128 * sizeof(float2);     // cotangent slots
+    auto *k = k_adjoint_pairs<N, PERIODIC, DB, BC, MIXED>;
+    const cudaError_t e = allow_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, 128, smem, c->stream>>>(fin, lam, coef, g, bc, lam_g, scale, c->adj_flag);
+    return cudaGetLastError();
+}
+
 template <int N, bool PERIODIC>
 cudaError_t pairs_n(vp_ctx *c, const float *fin, float *lam, const LineCoef<float> *coef,
                     const PairGeom &g, dim3 grid, const double *bc, double *lam_g, double scale)
 {
-    const bool db = g.axis >= 3 && lam_g;
-    int *sk = c->adj_flag;
-    constexpr size_t smem = (size_t)N * 128 * sizeof(float2);     // cotangent slots
-    if (db)
-        k_adjoint_pairs<N, PERIODIC, true, false, false><<<grid, 128, smem, c->stream>>>(
-            fin, lam, coef, g, bc, lam_g, scale, sk);
-    else if (bc)
-        k_adjoint_pairs<N, PERIODIC, false, true, false><<<grid, 128, smem, c->stream>>>(
-            fin, lam, coef, g, bc, lam_g, scale, sk);
-    else if (g.axis == 2 && g.mixed)
-        k_adjoint_pairs<N, PERIODIC, false, false, true><<<grid, 128, smem, c->stream>>>(
-            fin, lam, coef, g, bc, lam_g, scale, sk);
-    else
-        k_adjoint_pairs<N, PERIODIC, false, false, false><<<grid, 128, smem, c->stream>>>(
-            fin, lam, coef, g, bc, lam_g, scale, sk);
-    return cudaGetLastError();
+    if (g.axis >= 3 && lam_g)
+        return pairs_launch<N, PERIODIC, true, false, false>(c, fin, lam, coef, g, grid, bc, lam_g, scale);
+    if (bc)
+        return pairs_launch<N, PERIODIC, false, true, false>(c, fin, lam, coef, g, grid, bc, lam_g, scale);
+    if (g.axis == 2 && g.mixed)
+        return pairs_launch<N, PERIODIC, false, false, true>(c, fin, lam, coef, g, grid, bc, lam_g, scale);
+    return pairs_launch<N, PERIODIC, false, false, false>(c, fin, lam, coef, g, grid, bc, lam_g, scale);
 }
 
 template <int N>
@@ -846,6 +873,8 @@ cudaError_t rows_n(vp_ctx *c, const float *fin, float *lam, const LineCoef<float
 {
     constexpr int P = N + 4;
     const size_t smem = 4 * 2 * 32 * P * sizeof(float);
+    const cudaError_t e = allow_smem(k_adjoint_rows<N>, smem);
+    if (e != cudaSuccess) return e;
     const long long units = c->np * (N * N / 32);
     k_adjoint_rows<N><<<(unsigned)((units + 3) / 4), 128, smem, c->stream>>>(fin, lam, coef, c->np,
                                                                             lam_g, scale, c->adj_flag);
@@ -928,10 +957,14 @@ int vp_adjoint_pairs_ok(const vp_ctx *c, int axis)
     if (c->isdouble || !c->adj_flag) return 0;
     if (axis < 3) {
         const int n = c->n[axis];
-        return (n == 16 || n == 32) && c->nvc % 2 == 0 && c->np / n <= 65535;
+        // the two lines of a pair (v, v + 1) share their velocity along x or
+        // y (an even count of inner velocity cells); along z they may differ
+        const long long inner = axis == 0 ? (long long)c->nv[1] * c->nv[2] : (axis == 1 ? c->nv[2] : 2);
+        return (n == 16 || n == 32 || n == 48) && c->nvc % 2 == 0 && inner % 2 == 0 &&
+               c->np / n <= 65535;
     }
     const int n = c->nv[0];
-    return n == c->nv[1] && n == c->nv[2] && (n == 16 || n == 32) && c->np <= 65535;
+    return n == c->nv[1] && n == c->nv[2] && (n == 16 || n == 32 || n == 48) && c->np <= 0x7fffffffLL;
 }
 
 cudaError_t launch_adjoint_pairs(vp_ctx *c, const void *fin_, void *lam_, int axis,
@@ -977,21 +1010,28 @@ cudaError_t launch_adjoint_pairs(vp_ctx *c, const void *fin_, void *lam_, int ax
         const long long nparts = (g.units + 127) / 128;
         const dim3 grid((unsigned)nparts, (unsigned)outer);
         const LineCoef<float> *cf = coef + (size_t)axis * c->maxnv;
-        if (c->periodic_space)
+        if (c->periodic_space) {
+            if (n == 48) return pairs_n<48, true>(c, fin, lam, cf, g, grid, bc, nullptr, 0.0);
             return n == 32 ? pairs_n<32, true>(c, fin, lam, cf, g, grid, bc, nullptr, 0.0)
                            : pairs_n<16, true>(c, fin, lam, cf, g, grid, bc, nullptr, 0.0);
+        }
+        if (n == 48) return pairs_n<48, false>(c, fin, lam, cf, g, grid, bc, nullptr, 0.0);
         return n == 32 ? pairs_n<32, false>(c, fin, lam, cf, g, grid, bc, nullptr, 0.0)
                        : pairs_n<16, false>(c, fin, lam, cf, g, grid, bc, nullptr, 0.0);
     }
     const int va = axis - 3, n = c->nv[0];
     double *lg = lam_g ? lam_g + (size_t)va * c->np : nullptr;
-    if (va == 2) return n == 32 ? rows_n<32>(c, fin, lam, coef, lg, scale)
-                                : rows_n<16>(c, fin, lam, coef, lg, scale);
+    if (va == 2) {
+        if (n == 48) return rows_n<48>(c, fin, lam, coef, lg, scale);
+        return n == 32 ? rows_n<32>(c, fin, lam, coef, lg, scale)
+                       : rows_n<16>(c, fin, lam, coef, lg, scale);
+    }
     g.pd = n / 2;
     g.pm_hi = va == 0 ? n : (long long)n * n;
     g.vstride = va == 0 ? (long long)n * n : n;
     g.units = (long long)n * n / 2;
-    const dim3 grid((unsigned)((g.units + 127) / 128), (unsigned)c->np);
+    const dim3 grid((unsigned)c->np, (unsigned)((g.units + 127) / 128));
+    if (n == 48) return pairs_n<48, false>(c, fin, lam, coef, g, grid, nullptr, lg, scale);
     return n == 32 ? pairs_n<32, false>(c, fin, lam, coef, g, grid, nullptr, lg, scale)
                    : pairs_n<16, false>(c, fin, lam, coef, g, grid, nullptr, lg, scale);
 }

@@ -179,7 +179,7 @@ cudaError_t launch_kick_adjoint(vp_ctx *c, const void *fin, void *lam, int vaxis
                                 double tau, double *lam_g);
 // defer: leave dvol_v lam_rho in c->rho2 instead of adding it to lam_f
 cudaError_t launch_field_adjoint(vp_ctx *c, const double *lam_g, void *lam_f, bool defer);
-// FP32 packed register-line adjoint sweeps (line lengths 16/32, zero
+// FP32 packed register-line adjoint sweeps (line lengths 16/32/48, zero
 // whole-cell shift; skipped lines set c->adj_flag)
 int vp_adjoint_pairs_ok(const vp_ctx *c, int axis);
 // the three velocity-sweep adjoints of a half kick in one cube pass (FP32,

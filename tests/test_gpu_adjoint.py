@@ -1,5 +1,6 @@
 """GPU discrete adjoint against the FP64 oracle's adjoint (same frozen-branch
 rules) and against central finite differences of the GPU forward map."""
+import gc
 import math
 
 import numpy as np
@@ -67,12 +68,16 @@ def test_sweep_adjoint_matches_oracle(space_bc):
     ("f32", dict(n=(16, 32, 16), nv=(16, 16, 32)), "outflow"),
     ("f32", dict(n=(4, 2, 2), nv=(32, 32, 32)), "periodic"),
     ("f32", dict(n=(4, 4, 2), nv=(16, 16, 16)), "periodic"),
+    ("f32", dict(n=(48, 2, 2), nv=(2, 4, 6)), "periodic"),
+    ("f32", dict(n=(48, 2, 2), nv=(2, 4, 6)), "outflow"),
+    ("f32", dict(n=(2, 2, 1), nv=(48, 48, 48)), "periodic"),
 ])
 def test_register_adjoint_sweeps_match_oracle(dtype, shape, space_bc):
     """Line lengths served by the register-line adjoint kernels: FP64 lines
     of 16; FP32 packed line pairs of 16 and 32 along position axes (both
     boundary kinds, and pairs of z lines with different speeds) and along vx
-    and vy of 16^3 and 32^3 cubes, and the warp-staged vz rows."""
+    and vy of 16^3 and 32^3 cubes, and the warp-staged vz rows; the same for
+    lines of 48 (x lines, 48^3 cubes)."""
     w = I.small_maxwell(dtype=dtype, amp=0.3, space_bc=space_bc, **shape)
     w = w.replace(box_lo=(-0.5,) * 3, box_hi=(0.5,) * 3)
     grid = O.Grid.of(w)
@@ -199,6 +204,33 @@ def test_adjoint_step_48_cubes_match_oracle(states):
     sim.close()
 
 
+@pytest.mark.gpu
+@pytest.mark.parametrize("nx", [16, 32, 48])
+def test_adjoint_step_fp32_x_lines_match_oracle(nx):
+    """FP32 adjoint step on x lines of 16, 32 and 48 (the line-pair x-drift
+    adjoint with the density cotangent added as it loads the cotangent)
+    against the oracle's adjoint step.  The outer v_x cells shift by 1.44
+    cells: the pair kernel leaves those lines to the fix-up sweep, which must
+    see their density cotangent too."""
+    w = I.small_maxwell(n=(nx, 2, 2), nv=(4, 4, 6), dtype="f32", amp=0.3, G=20.0)
+    w = w.replace(box_lo=(-0.5, -0.05, -0.05), box_hi=(0.5, 0.05, 0.05), dt_fixed=0.48 / nx)
+    rng = np.random.default_rng(12)
+    f0 = (I.initial_condition(w, np.float64) * (1 + 0.2 * rng.random(w.shape))).astype(np.float32)
+    sim, f = gpu_sim(w, f0)
+    g0 = sim.field()[2]
+    lam_f = torch.from_numpy(rng.normal(size=w.shape).astype(np.float32)).to(DEV)
+    lam_g = torch.from_numpy(rng.normal(size=(3,) + w.n)).to(DEV)
+    lf0, lg0 = lam_f.cpu().numpy().astype(np.float64), lam_g.cpu().numpy()
+    sim.adjoint_step(torch.from_numpy(f0).to(DEV), g0, lam_f, lam_g)
+    f64 = f0.astype(np.float64)
+    osim = O.Simulation(f64, O.Grid.of(w), O.Params.of(w))
+    rf, rg = O.adjoint_step(osim, f64, osim.g, lf0, lg0)
+    got_f, got_g = lam_f.cpu().numpy().astype(np.float64), lam_g.cpu().numpy()
+    assert np.abs(got_f - rf).sum() / np.abs(rf).sum() <= 2e-5
+    assert np.abs(got_g - rg).sum() / np.abs(rg).sum() <= 2e-5
+    sim.close()
+
+
 def _mode_f0(w, amps, dtype):
     """f0(A) = rho_bar (1 + sum_m A_m cos(k_m.x + th_m)) M(v), in torch."""
     fields = torch.from_numpy(I.mode_fields(w)).to(DEV)
@@ -315,6 +347,8 @@ def test_jeans48_modes8_trajectory_gradient_matches_fd():
     w = I.large_c5()
     nsteps, every = 20, 10
     amps0 = np.array([m[1] for m in w.modes])
+    gc.collect()
+    torch.cuda.empty_cache()
     f = torch.zeros(w.shape, dtype=torch.float32, device=DEV)
     sim = VlasovPoisson(config_of(w), f)
     f0 = _fill_mode_f0(w, amps0, torch.empty_like(f)).requires_grad_(True)
