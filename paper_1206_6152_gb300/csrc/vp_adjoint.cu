@@ -856,66 +856,69 @@ int vp_set_adjoint_states(vp_ctx *c, int mode)
 
 namespace {
 
-// sweeps 0..2 (K1) of the replay from S0 into dst, in one launch sequence
-int replay_k1(vp_ctx *c, const void *S0, void *dst, const void *k1)
+// the first nsweeps (2 or 3) velocity sweeps of a half kick with table
+// coef from src into dst, in one launch sequence
+int replay_kick(vp_ctx *c, const void *src, void *dst, const void *coef, int nsweeps)
 {
-    void *src = const_cast<void *>(S0);
+    void *s = const_cast<void *>(src);
     if (vp_kick_fast_ok(c)) {
-        VP_CUDA_TRY(launch_kick_fast(c, src, k1, nullptr, 3, 0, dst));
+        VP_CUDA_TRY(launch_kick_fast(c, s, coef, nullptr, nsweeps, 0, dst));
     } else if (vp_kick_big_ok(c)) {
-        VP_CUDA_TRY(launch_kick_big(c, src, k1, nullptr, 3, 0, dst));
+        VP_CUDA_TRY(launch_kick_big(c, s, coef, nullptr, nsweeps, 0, dst));
     } else {
-        VP_CUDA_TRY(cudaMemcpyAsync(dst, S0, (size_t)c->ncells * c->esize, cudaMemcpyDeviceToDevice,
+        VP_CUDA_TRY(cudaMemcpyAsync(dst, src, (size_t)c->ncells * c->esize, cudaMemcpyDeviceToDevice,
                                     c->stream));
-        VP_CUDA_TRY(launch_kick(c, dst, k1, nullptr, 3, 0));
+        VP_CUDA_TRY(launch_kick(c, dst, coef, nullptr, nsweeps, 0));
     }
     return VP_OK;
 }
 
-// The adjoint step with two scratch states X, Y: the sweep inputs S1..S8
-// are recomputed from S0 = f_start in four partial replays, each leaving two
-// consecutive inputs in X and Y: (S7, S8) [and g^{n+1} on the way], (S5,
-// S6), (S3, S4), (S1, S2).  The adjoint sweeps run in reverse order between
-// the replays.
+// The adjoint step with two scratch states X, Y.  The sweep inputs S1..S8
+// are recomputed from S0 = f_start, keeping at most two at a time, so that
+// each adjoint sweep finds its input in X or Y (or S0):
+//   S0 -> S3 -> S4 -> S5 -> S6 (Y, kept) [g^{n+1}];  S8 from S6 (vx and vy
+//   in one pass, X): vz;  S7 from S6 (X): vy;  S6: vx;  field
+//   S0 -> S3 -> S4 (Y) -> S5 (X): x;  S4: y         (fused y+z: S3 again)
+//   S0 -> S3 (X): z
+//   S2 from S0 (vx and vy, X): vz;  S1 from S0 (X): vy;  S0: vx
 int adjoint_step_two_states(vp_ctx *c, const void *S0, void *lambda_f, double *lambda_g,
                             const void *k1, const double *tau_ptr, double dt, double amax)
 {
     void *X = c->adj_states[0], *Y = c->adj_states[1];
     const double tau = 0.5 * dt;
-    // replay to (S7, S8); the density of S6 gives g^{n+1}
-    TRY(replay_k1(c, S0, X, k1));                                                 // X = S3
+    const bool yz = amax < 1.0 && vp_drift_adjoint_yz_ok(c);
+    // replay to S6; its density gives g^{n+1}
+    TRY(replay_kick(c, S0, X, k1, 3));                                            // X = S3
     VP_CUDA_TRY(launch_sweep_into(c, X, Y, 2, c->coef_drift, amax));              // Y = S4
     VP_CUDA_TRY(launch_sweep_into(c, Y, X, 1, c->coef_drift, amax));              // X = S5
     VP_CUDA_TRY(launch_sweep_into(c, X, Y, 0, c->coef_drift, amax));              // Y = S6
     VP_CUDA_TRY(launch_density(c, Y, c->rho2));
     VP_CUDA_TRY(launch_field_solve(c, c->rho2, c->adj_g));
     VP_CUDA_TRY(launch_coef_kick(c, c->adj_g, tau_ptr, 0.5, c->coef_kick2));
+    // K2 reversed with S6 kept in Y
+    TRY(replay_kick(c, Y, X, c->coef_kick2, 2));                                  // X = S8
+    VP_CUDA_TRY(launch_kick_adjoint(c, X, lambda_f, 2, c->coef_kick2, tau, lambda_g));
     VP_CUDA_TRY(launch_sweep_into(c, Y, X, 3, c->coef_kick2, amax));              // X = S7
-    VP_CUDA_TRY(launch_sweep_into(c, X, Y, 4, c->coef_kick2, amax));              // Y = S8
-    VP_CUDA_TRY(launch_kick_adjoint(c, Y, lambda_f, 2, c->coef_kick2, tau, lambda_g));
     VP_CUDA_TRY(launch_kick_adjoint(c, X, lambda_f, 1, c->coef_kick2, tau, lambda_g));
-    // replay to (S5, S6)
-    TRY(replay_k1(c, S0, X, k1));
-    VP_CUDA_TRY(launch_sweep_into(c, X, Y, 2, c->coef_drift, amax));
-    VP_CUDA_TRY(launch_sweep_into(c, Y, X, 1, c->coef_drift, amax));              // X = S5
-    VP_CUDA_TRY(launch_sweep_into(c, X, Y, 0, c->coef_drift, amax));              // Y = S6
     VP_CUDA_TRY(launch_kick_adjoint(c, Y, lambda_f, 0, c->coef_kick2, tau, lambda_g));
     VP_CUDA_TRY(launch_field_adjoint(c, lambda_g, lambda_f, true));
+    // the drifts reversed: replay to S5 keeping S4
+    TRY(replay_kick(c, S0, X, k1, 3));                                            // X = S3
+    VP_CUDA_TRY(launch_sweep_into(c, X, Y, 2, c->coef_drift, amax));              // Y = S4
+    VP_CUDA_TRY(launch_sweep_into(c, Y, X, 1, c->coef_drift, amax));              // X = S5
     VP_CUDA_TRY(launch_drift_adjoint(c, X, lambda_f, 0, c->coef_drift, c->rho2));
-    // replay to S3 (and S4, unless the fused y+z adjoint recomputes it)
-    TRY(replay_k1(c, S0, X, k1));                                                 // X = S3
-    if (amax < 1.0 && vp_drift_adjoint_yz_ok(c)) {
+    if (!yz) VP_CUDA_TRY(launch_drift_adjoint(c, Y, lambda_f, 1, c->coef_drift, nullptr));
+    TRY(replay_kick(c, S0, X, k1, 3));                                            // X = S3
+    if (yz) {
         VP_CUDA_TRY(launch_drift_adjoint_yz(c, X, lambda_f, c->coef_drift));
     } else {
-        VP_CUDA_TRY(launch_sweep_into(c, X, Y, 2, c->coef_drift, amax));          // Y = S4
-        VP_CUDA_TRY(launch_drift_adjoint(c, Y, lambda_f, 1, c->coef_drift, nullptr));
         VP_CUDA_TRY(launch_drift_adjoint(c, X, lambda_f, 2, c->coef_drift, nullptr));
     }
-    // replay to (S1, S2)
+    // K1 reversed
     VP_CUDA_TRY(cudaMemsetAsync(lambda_g, 0, sizeof(double) * 3 * c->np, c->stream));
+    TRY(replay_kick(c, S0, X, k1, 2));                                            // X = S2
+    VP_CUDA_TRY(launch_kick_adjoint(c, X, lambda_f, 2, k1, tau, lambda_g));
     VP_CUDA_TRY(launch_sweep_into(c, S0, X, 3, k1, amax));                        // X = S1
-    VP_CUDA_TRY(launch_sweep_into(c, X, Y, 4, k1, amax));                         // Y = S2
-    VP_CUDA_TRY(launch_kick_adjoint(c, Y, lambda_f, 2, k1, tau, lambda_g));
     VP_CUDA_TRY(launch_kick_adjoint(c, X, lambda_f, 1, k1, tau, lambda_g));
     VP_CUDA_TRY(launch_kick_adjoint(c, S0, lambda_f, 0, k1, tau, lambda_g));
     return VP_OK;

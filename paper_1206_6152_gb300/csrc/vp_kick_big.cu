@@ -376,15 +376,16 @@ cudaError_t persistent_grid(K kern, int threads, size_t smem, long long nunits, 
 
 }  // namespace
 
-// The fused kick (6 sweeps: A, B, C) or one half kick (3 sweeps: A, C
-// without its vy sweep) of FP32 cubes of edge 48, from f into fo (fo == f
-// in place).  Returns cudaErrorNotSupported for other sweep runs.
+// The fused kick (6 sweeps: A, B, C), one half kick (3 sweeps: A, C
+// without its vy sweep) or the vx and vy sweeps of a half kick (2 sweeps:
+// A) of FP32 cubes of edge 48, from f into fo (fo == f in place).  Returns
+// cudaErrorNotSupported for other sweep runs.
 cudaError_t launch_kick_big3(vp_ctx *c, float *f, const LineCoef<float> *ca,
                              const LineCoef<float> *cb, int nsweeps, int first_axis, float *fo)
 {
     constexpr int N = 48;
     typedef Big3<N> B;
-    if (first_axis != 0 || (nsweeps != 6 && nsweeps != 3)) return cudaErrorNotSupported;
+    if (first_axis != 0 || (nsweeps != 6 && nsweeps != 3 && nsweeps != 2)) return cudaErrorNotSupported;
     const long long nunits = c->np * B::NU;
     cudaError_t e;
     unsigned grid;
@@ -396,6 +397,11 @@ cudaError_t launch_kick_big3(vp_ctx *c, float *f, const LineCoef<float> *ca,
     k_kick_pass_a<N><<<grid, B::NT, smem_a, c->stream>>>(f, ca, nunits, &c->sc->lost, fo);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[1], c->stream)) != cudaSuccess) return e;
+    if (nsweeps == 2) {             // vx and vy only: pass A
+        if (ev && (e = cudaEventRecord(ev[2], c->stream)) != cudaSuccess) return e;
+        if (ev && (e = cudaEventRecord(ev[3], c->stream)) != cudaSuccess) return e;
+        return cudaSuccess;
+    }
     if (nsweeps == 6) {
         if ((e = persistent_grid(k_kick_pass_b<N>, B::NT, smem_bc, nunits, grid)) != cudaSuccess) return e;
         k_kick_pass_b<N><<<grid, B::NT, smem_bc, c->stream>>>(fo, ca, cb, nunits, &c->sc->lost, fo);
