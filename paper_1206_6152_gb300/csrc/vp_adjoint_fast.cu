@@ -35,9 +35,10 @@
 //    copied by cp.async into the thread's shared-memory slots and streamed
 //    from there (a warp reads two 128-byte rows per load).  The x-drift
 //    adjoint can add the broadcast of the density cotangent on load.
-//  * k_adjoint_rows: the vz sweep; each warp stages 32 rows of the state and
-//    of the cotangent in shared memory with coalesced 16-byte loads, one row
-//    per lane, and writes the rows back the same way.
+//  * k_adjoint_rows: the vz sweep; persistent warps each stage 32 rows of
+//    the state and of the cotangent in shared memory by 16-byte asynchronous
+//    copies (the next 32 rows prefetched into L2 meanwhile), sweep one row
+//    per lane, and write the rows back with coalesced 16-byte stores.
 //  * k_kick_adjoint_zy: the vz and then the vy adjoint of a half kick on the
 //    same staged rows (a warp holds whole vx planes), followed by the vx
 //    adjoint as line pairs: the cotangent crosses HBM twice for three sweeps.
@@ -566,7 +567,62 @@ __device__ __forceinline__ void row_store(float *row, const float (&x)[N])
         *reinterpret_cast<float4 *>(row + c) = make_float4(x[c], x[c + 1], x[c + 2], x[c + 3]);
 }
 
-// vz sweep of FP32 cubes of edge N (16 or 32): warp units of 32 rows
+// asynchronous 16-byte copy global -> shared, and an asynchronous prefetch
+// of [p, p + bytes) into L2 (16-byte aligned, bytes a multiple of 16)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// 32 contiguous rows of N floats (global) into a tile of pitch P, in array
+// order, by 16-byte asynchronous copies (the caller waits)
+template <int N, int P>
+__device__ __forceinline__ void rows_in_async(float *tile, const float *g, int lane)
+{
+    constexpr int Q = N / 4;
+#pragma unroll
+    for (int e = lane; e < 32 * Q; e += 32) {
+        const int r = e / Q, c = 4 * (e % Q);
+        cp_async16(tile + r * P + c, g + r * N + c);
+    }
+}
+
+// one tile row to registers in upwind order (rev: the row mirrored) and back
+template <int N>
+__device__ __forceinline__ void row_load_dir(float (&x)[N], const float *row, bool rev)
+{
+    if (!rev) {
+        row_load<N>(x, row);
+        return;
+    }
+#pragma unroll
+    for (int c = 0; c < N; c += 4) {
+        const float4 a = *reinterpret_cast<const float4 *>(row + N - 4 - c);
+        x[c] = a.w; x[c + 1] = a.z; x[c + 2] = a.y; x[c + 3] = a.x;
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void row_store_dir(float *row, const float (&x)[N], bool rev)
+{
+    if (!rev) {
+        row_store<N>(row, x);
+        return;
+    }
+#pragma unroll
+    for (int c = 0; c < N; c += 4)
+        *reinterpret_cast<float4 *>(row + N - 4 - c) = make_float4(x[c + 3], x[c + 2], x[c + 1], x[c]);
+}
+
+// vz sweep of FP32 cubes of edge N (16, 32 or 48): persistent warps taking
+// units of 32 rows in turn, each staged in shared memory by 16-byte
+// asynchronous copies (array order; a row with u_z < 0 is read mirrored)
+// while the next unit's rows are prefetched into L2
 template <int N>
 __global__ void __launch_bounds__(128) k_adjoint_rows(const float *__restrict__ fin,
                                                      float *__restrict__ lam,
@@ -575,37 +631,49 @@ __global__ void __launch_bounds__(128) k_adjoint_rows(const float *__restrict__ 
                                                      double scale, int *skipped)
 {
     constexpr int P = N + 4, UPC = N * N / 32;   // pitch, units per cube
+    constexpr unsigned UB = 32 * N * sizeof(float);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *tf = reinterpret_cast<float *>(smem_raw) + warp * 2 * 32 * P;
     float *tl = tf + 32 * P;
-    const long long unit = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
-    if (unit >= np * UPC) return;
-    const long long cell = unit / UPC;
-    const LineCoef<float> cf = coef[cell * 3 + 2];
-    if ((cf.code >> 1) != 0) {
-        if (lane == 0) atomicExch(skipped, 1);
-        return;
+    const long long nunits = np * UPC;
+    const long long ustride = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long unit = (long long)blockIdx.x * (blockDim.x >> 5) + warp; unit < nunits;
+         unit += ustride) {
+        const long long cell = unit / UPC;
+        const LineCoef<float> cf = coef[cell * 3 + 2];
+        const long long next = unit + ustride;
+        if (lane == 0 && next < nunits) {
+            prefetch_l2(fin + next * 32 * N, UB);
+            prefetch_l2(lam + next * 32 * N, UB);
+        }
+        if ((cf.code >> 1) != 0) {
+            if (lane == 0) atomicExch(skipped, 1);
+            continue;
+        }
+        const bool neg = cf.code & 1;
+        const long long off = unit * 32 * N;          // 32 contiguous rows
+        __syncwarp();       // the previous unit's tiles are read out
+        rows_in_async<N, P>(tf, fin + off, lane);
+        rows_in_async<N, P>(tl, lam + off, lane);
+        cp_async_wait_all();
+        __syncwarp();
+        float f[N], l[N];
+        row_load_dir<N>(f, tf + lane * P, neg);
+        row_load_dir<N>(l, tl + lane * P, neg);
+        int arg;
+        float lfinf;
+        const float db = adjoint_scalar<N, false, true>(f, l, cf, arg, lfinf);
+        row_store_dir<N>(tl + lane * P, l, neg);
+        tl[lane * P + (neg ? N - 1 - arg : arg)] += lfinf;
+        __syncwarp();
+        rows_out<N, P>(lam + off, tl, false, lane);
+        if (lam_g) {
+            float sum = db;
+            for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
+            if (lane == 0 && sum != 0.f) atomicAdd(lam_g + cell, (double)sum * scale);
+        }
     }
-    const bool neg = cf.code & 1;
-    const long long off = unit * 32 * N;          // 32 contiguous rows
-    rows_in<N, P>(tf, fin + off, neg, lane);
-    rows_in<N, P>(tl, lam + off, neg, lane);
-    __syncwarp();
-    float f[N], l[N];
-    row_load<N>(f, tf + lane * P);
-    row_load<N>(l, tl + lane * P);
-    int arg;
-    float lfinf;
-    const float db = adjoint_scalar<N, false, true>(f, l, cf, arg, lfinf);
-    row_store<N>(tl + lane * P, l);
-    tl[lane * P + arg] += lfinf;
-    __syncwarp();
-    rows_out<N, P>(lam + off, tl, neg, lane);
-    if (!lam_g) return;
-    float s = db;
-    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
-    if (lane == 0 && s != 0.f) atomicAdd(lam_g + cell, (double)s * scale);
 }
 
 // The vz and vy adjoints of a half kick in one pass: each warp takes 32
@@ -833,6 +901,22 @@ __global__ void __launch_bounds__(AdjYZ<N>::NT, 2) k_drift_adjoint_yz(
     }
 }
 
+// persistent warps: as many CTAs of 128 threads as fit on the SMs at once
+// (the kernel's register and shared-memory limits), or fewer where there
+// are fewer units of four warps
+template <class K>
+unsigned persistent_grid(K kernel, size_t smem, long long units)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, smem) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const long long g = (units + 3) / 4, cap = (long long)per_sm * vp_sm_count();
+    return (unsigned)(g < cap ? g : cap);
+}
+
 // dynamic shared memory above the default 48 KB (static included) must be
 // allowed per kernel before its launch
 template <class K>
@@ -876,7 +960,7 @@ cudaError_t rows_n(vp_ctx *c, const float *fin, float *lam, const LineCoef<float
     const cudaError_t e = allow_smem(k_adjoint_rows<N>, smem);
     if (e != cudaSuccess) return e;
     const long long units = c->np * (N * N / 32);
-    k_adjoint_rows<N><<<(unsigned)((units + 3) / 4), 128, smem, c->stream>>>(fin, lam, coef, c->np,
+    k_adjoint_rows<N><<<persistent_grid(k_adjoint_rows<N>, smem, units), 128, smem, c->stream>>>(fin, lam, coef, c->np,
                                                                             lam_g, scale, c->adj_flag);
     return cudaGetLastError();
 }
