@@ -369,7 +369,7 @@ struct PairGeom {
 // of thread t at j * 128 + t: conflict-free) and streamed from there, which
 // keeps the kernel at 128 registers (16 warps per SM).
 template <int N, bool PERIODIC, bool DB, bool BC, bool MIXED>
-__global__ void __launch_bounds__(128, N <= 32 ? 4 : 2) k_adjoint_pairs(const float *__restrict__ fin,
+__global__ void __launch_bounds__(128, N <= 32 ? 4 : 3) k_adjoint_pairs(const float *__restrict__ fin,
                                                       float *__restrict__ lam,
                                                       const LineCoef<float> *__restrict__ coef,
                                                       PairGeom g, const double *__restrict__ bc,
