@@ -441,16 +441,14 @@ def roofline_of(w, avg, esize):
     kernel against the measured HBM peak."""
     bytes_rw = 2 * w.cells * esize
     avg = dict(avg)
-    if avg.get("kick_a", 0.0) > 0.0:
-        passes = PASSES_BIG
+    # the kick: three slab passes (48^3 cubes) or one cube pass
+    kicks = PASSES_BIG[:3] if avg.get("kick_a", 0.0) > 0.0 else PASSES_FUSED[:1]
+    if avg["drift_y"] < 0.02 * avg["drift_z"]:          # z and y drifts fused (slot 1)
+        avg["drift_yz"] = avg["drift_z"]
+        drifts = PASSES_FUSED[1:]
     else:
-        if avg["drift_y"] < 0.02 * avg["drift_z"]:      # z and y drifts fused (slot 1)
-            avg["drift_yz"] = avg["drift_z"]
-            passes = PASSES_FUSED
-        else:
-            passes = (("kick6", "k_kick6", "{w}:kick6"), ("drift_z", "k_drift_fast", "{w}:drift_z"),
-                      ("drift_y", "k_drift_fast", "{w}:drift_y"),
-                      ("drift_x", "k_drift_fast", "{w}:drift_x"))
+        drifts = PASSES_BIG[3:]
+    passes = kicks + drifts
     peak, peak_src = load_peaks()
     per = {slot: {"kernel": k, "ms": round(avg[slot], 4),
                   "achieved_gbs": round(bytes_rw / (avg[slot] / 1e3) / 1e9, 1)} for slot, k, _ in passes}
