@@ -203,6 +203,10 @@ __global__ void __launch_bounds__(Big3<N>::NT, 2) k_kick_pass_b(
         const LineCoef<float> c1 = ca[c * 3 + 2], c2 = cb[c * 3];
         float *gd = dst + c * NC;
         const long long un = u + gridDim.x;
+        // the next slab (48 runs of 8 rows, 1.5 KB each) into L2 ahead of
+        // its copies, which start only once this slab's vx lines are read
+        if (t < N && un < nunits)
+            prefetch_l2(src + (un / NU) * NC + (long long)t * N * N + (un % NU) * S * N, S * N * 4);
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();
         if (whole_cell(c1) || whole_cell(c2)) {
