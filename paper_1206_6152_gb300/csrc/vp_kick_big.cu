@@ -25,16 +25,17 @@
 //      staged by asynchronous copies, cp.async or TMA, read three times
 //      their bytes from DRAM, whatever their L2 eviction policy; plain loads
 //      read them once.)
-//   B: the slab (48 vx planes x 8 rows of 192 bytes) is copied into the tile
-//      with 16-byte cp.async copies; the vz sweep reads its row pairs from
+//   B: the slab (48 vx planes x 8 rows of 192 bytes) is prefetched into L2
+//      one unit ahead and copied into the tile with 16-byte cp.async
+//      copies; the vz sweep reads its row pairs from
 //      the tile and writes them back; the vx line pairs are read from the
 //      tile, the copies of the CTA's next slab start, and the vx lines are
 //      swept and stored to global memory.
 //   C: the vy line pairs are read from global memory (a warp reads 192
 //      contiguous bytes per row), swept and written to the tile; the vz
-//      sweep takes row pairs from the tile and writes them back; the CTA's
-//      next slab (73.7 KB, contiguous) is fetched into L2 by a bulk
-//      prefetch, and the tile is copied out with 16-byte stores that cover
+//      sweep takes row pairs from the tile and writes them back, while the
+//      CTA's next slab (73.7 KB, contiguous) is fetched into L2 by a bulk
+//      prefetch; the tile is copied out with 16-byte stores that cover
 //      contiguous memory.
 //
 // A unit whose cube has a whole-cell shift in one of the pass's sweeps
@@ -321,6 +322,11 @@ __global__ void __launch_bounds__(Big3<N>::NT, 2) k_kick_pass_c(
 #pragma unroll
         for (int j = 0; j < N; ++j) *reinterpret_cast<float2 *>(tile + pl * PP + j * RP + pk) = x[j];
         __syncthreads();
+        // the next slab into L2 while this one's vz rows are swept and the
+        // tile is copied out
+        if (t < 4 && un < nunits)
+            prefetch_l2(src + (un / NU) * NC + (long long)(un % NU) * S * N * N + t * (S * N * N / 4),
+                        S * N * N);
         {
             // sweep 2 (vz): rows (vy = rj, planes rl and rl + S/2), in place
             float *ra = tile + rl * PP + rj * RP, *rb = ra + (S / 2) * PP;
@@ -341,10 +347,6 @@ __global__ void __launch_bounds__(Big3<N>::NT, 2) k_kick_pass_c(
             }
         }
         __syncthreads();
-        // the next slab into L2 while this one is copied out
-        if (t < 4 && un < nunits)
-            prefetch_l2(src + (un / NU) * NC + (long long)(un % NU) * S * N * N + t * (S * N * N / 4),
-                        S * N * N);
         {
             constexpr int Q = N / 4, PER_L = N * Q, CHUNKS = S * PER_L;
             float *g = gd + (long long)i0 * N * N;
