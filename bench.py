@@ -54,6 +54,10 @@ def parse(argv=None):
     p.add_argument("--extra-workload", default="jeans32_f32",
                    help="second FP32 line, also timed in FP64 storage ('' for none)")
     p.add_argument("--cpu-sample", type=float, default=1.0 / 64)
+    p.add_argument("--slabs", type=int, default=2,
+                   help="x slabs of the slab-decomposition leg (all in this process)")
+    p.add_argument("--slab-workload", default="jeans32_f32")
+    p.add_argument("--slab-steps", type=int, default=5, help="0: no slab-decomposition leg")
     p.add_argument("--record-traffic", metavar="CSV", default="",
                    help="write profiles/traffic.json entries for --workload from an ncu --csv "
                         "launch list with dram__bytes_read.sum and dram__bytes_write.sum, taken "
@@ -550,6 +554,10 @@ def run_ours(args, ranks: Ranks):
     if args.extra_workload not in ("", "none") and args.extra_workload != args.workload:
         extra = time_extra(args, dev, stream, ranks)
 
+    slabs = None
+    if args.slab_steps > 0 and args.slabs > 0 and ranks.world == 1:
+        slabs = time_slabs(args, dev, stream)
+
     adjoint = []
     if args.adjoint_steps > 0:
         for aw in [x for x in args.adjoint_workloads.split(",") if x]:
@@ -571,7 +579,7 @@ def run_ours(args, ranks: Ranks):
                    "l2": "inputs larger than L2 (f is %.1f GB)" % (w.cells * esize / 1e9),
                    "parallelism": "replicas" if ranks.world > 1 else "single GPU"},
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
-        "extra": extra, "adjoint": adjoint, "cpu_baseline": cpu,
+        "extra": extra, "slabs": slabs, "adjoint": adjoint, "cpu_baseline": cpu,
     }
     return out
 
@@ -600,6 +608,67 @@ def time_extra(args, dev, stream, ranks):
         del f
         torch.cuda.empty_cache()
     return out
+
+
+def time_slabs(args, dev, stream):
+    """The split step over x slabs of position space (sharded.py) with all
+    slabs in this process on one GPU, exchanging by direct copies: the
+    single-context step plus what the decomposition adds (the ghosted x
+    drift, the halo planes, the reduction of the line maxima, the gathered
+    density and a field solve per slab, host-side orchestration and one host
+    read of dt per step).  Wall clock between synchronisations; the ghosted
+    x drift alone between CUDA events on the slabs' stream."""
+    import torch
+    from paper_1206_6152_gb300 import inputs as I
+    from paper_1206_6152_gb300.sharded import LibrarySlab, LocalExchange, ShardedStep
+    from paper_1206_6152_gb300.vlasov import config_of
+    w = I.WORKLOADS[args.slab_workload]()
+    R = args.slabs
+    if w.n[0] % R:
+        return {"workload": w.name, "unavailable": f"{w.n[0]} x planes do not split into {R} slabs"}
+    torch.cuda.empty_cache()
+    f, _ = make_f(w, dev)
+    cfg = config_of(w)
+    nx = w.n[0] // R
+    slabs = [LibrarySlab(cfg, r * nx, f[r * nx:(r + 1) * nx], stream) for r in range(R)]
+    try:
+        step = ShardedStep(slabs, LocalExchange())
+        k = args.slab_steps
+        step.step(3)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        step.step(k)
+        torch.cuda.synchronize(dev)
+        ms = 1e3 * (time.perf_counter() - t0) / k
+        # the ghosted x drift of one slab, timed alone
+        s0 = slabs[0]
+        G = step.nghost(step.dt)
+        lo, hi = s0.planes(nx - G, nx), s0.planes(0, G)
+        lmax = s0.line_max_x()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.drift_x(step.dt, lo, hi, G, lmax)
+        e0.record(stream)
+        for _ in range(k):
+            s0.drift_x(step.dt, lo, hi, G, lmax)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        dx_ms = e0.elapsed_time(e1) / k
+        slab_bytes = 2 * (w.cells // R) * f.element_size()
+        peak, _ = load_peaks()
+        return {"workload": w.name, "slabs": R, "planes_per_slab": nx, "ghost_planes": G,
+                "ms_per_step": round(ms, 3), "value": w.cells / (ms / 1e3), "unit": UNIT,
+                "drift_x_ghosted": {"ms": round(dx_ms, 4),
+                                    "achieved_gbs": round(slab_bytes / (dx_ms / 1e3) / 1e9, 1),
+                                    "frac": round(slab_bytes / (dx_ms / 1e3) / 1e9 / peak, 4),
+                                    "bytes": "f of the slab read and written once (ghost reads "
+                                             "not counted)"},
+                "note": "all slabs on one GPU in one process (direct copies for the exchanges); "
+                        "wall clock per step between synchronisations"}
+    finally:
+        for s in slabs:
+            s.close()
+        del f
+        torch.cuda.empty_cache()
 
 
 def time_adjoint(args, name, dev, stream):

@@ -223,7 +223,7 @@ int vp_functional(vp_ctx *ctx, int kind, const double *target, void *lambda_f,
  * velocity space kept whole).  A slab's context is made by vp_init with the
  * slab's own grid (n[0] = its planes, box_lo[0]/box_hi[0] its extent, the
  * same cell widths).  Kicks and the y and z drifts are slab-local
- * (vp_sweep); the x drift needs the neighbours' planes and the maximum of
+ * (vp_kick, vp_drift_yz); the x drift needs the neighbours' planes and the maximum of
  * every whole x line (vp_line_max_x, vp_drift_x_ghosted); the field is
  * solved from the gathered density by a field-only context of the whole
  * grid (vp_field_init, vp_field_solve) on every GPU, and the slab's part of
@@ -232,6 +232,21 @@ int vp_functional(vp_ctx *ctx, int kind, const double *target, void *lambda_f,
  * line maxima, halo planes, all-gather of the density).  Periodic position
  * space only.
  * ------------------------------------------------------------------- */
+
+/* The velocity sweeps of a half kick, T_vx T_vy T_vz (Sec. 2.1, Eq.
+ * (adv_vel)), in place, with the context's acceleration (vp_set_accel) and
+ * duration tau1; with tau2 != 0 followed by a second half kick of duration
+ * tau2 with the same acceleration (K2 of step n and K1 of step n+1, which
+ * share g^{n+1}), in the passes over f of the step's own fused kick (one
+ * pass for cubes of 16 and 32, three for 48).  Results as six vp_sweep
+ * calls.  VP_ERR_ARG for a non-finite tau; asynchronous. */
+int vp_kick(vp_ctx *ctx, double tau1, double tau2);
+
+/* The z then the y drift, T_z(tau) T_y(tau) (Sec. 2.1, Eq. (adv_xpos)), in
+ * place, in one pass where the fused drift kernel applies (FP32, N_y = N_z
+ * in {16, 32}, no whole-cell shift), else one pass each.  Results as two
+ * vp_sweep calls.  VP_ERR_ARG for a non-finite tau; asynchronous. */
+int vp_drift_yz(vp_ctx *ctx, double tau);
 
 /* Per-line maxima along x of the context's f: lmax_dev[(y, z, v)] = max(0,
  * max_i f[i][y][z][v]) over the slab's planes, laid out [ny][nz][nvx][nvy]

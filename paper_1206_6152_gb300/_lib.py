@@ -22,7 +22,7 @@ EXPORTS = (
     "vp_adjoint_step", "vp_field_adjoint", "vp_functional", "vp_destroy", "vp_error_string",
     "vp_profile_step", "vp_stats", "vp_sweep_adjoint", "vp_moments_noalloc",
     "vp_set_adjoint_states", "vp_check", "vp_debug_fail_alloc", "vp_line_max_x",
-    "vp_drift_x_ghosted", "vp_field_init", "vp_field_solve",
+    "vp_drift_x_ghosted", "vp_field_init", "vp_field_solve", "vp_kick", "vp_drift_yz",
 )
 PROFILE_SLOTS = 11
 PROFILE_NAMES = ("kick6", "drift_z", "drift_y", "drift_x", "density", "field", "tables", "step",
@@ -98,6 +98,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "vp_drift_x_ghosted": (i, [vp, d, vp, vp, i, vp]),
             "vp_field_init": (i, [ctypes.POINTER(vp_config), vp, ctypes.POINTER(vp)]),
             "vp_field_solve": (i, [vp, vp, vp, dp]),
+            "vp_kick": (i, [vp, d, d]),
+            "vp_drift_yz": (i, [vp, d]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)

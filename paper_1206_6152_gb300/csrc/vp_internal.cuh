@@ -34,7 +34,7 @@ struct DevScalars {
     double t;           // simulated time
     double lost;        // phase-space sum of f that left (unscaled)
     double amax;        // max_l,x |g_l| / dv_l of the last dt evaluation
-    double pad[4];
+    double pad[6];      // per-call scalars of the entry points (stream-ordered)
 };
 
 struct FFTAxis {

@@ -19,7 +19,8 @@ Per step (Eq. integration, as the single-GPU step):
     line maxima along x -> all-reduce max;  G edge planes -> neighbours
     x drift (dt) of each slab with its ghost planes and the whole lines' maxima
     density of each slab -> all-gather -> phi, g^{n+1} and the next dt
-    K2: vx, vy, vz sweeps (dt/2) with g^{n+1}
+    K2: vx, vy, vz sweeps (dt/2) with g^{n+1}  (with the next step's K1 in
+        the same passes, as in the single-GPU step)
 
 Each slab's work goes through a backend (`LibrarySlab`: the CUDA library's
 slab context and a field-only context of the whole grid); the exchanges go
@@ -162,13 +163,13 @@ class LibrarySlab:
             self._fctx = ctypes.c_void_p()
         self.sim.close()
 
-    def kick(self, tau: float) -> None:
-        for axis in (3, 4, 5):
-            self.sim.sweep(axis, tau)
+    def kick(self, tau: float, tau_next: float = 0.0) -> None:
+        """A half kick of duration tau; with tau_next, the next step's first
+        half kick after it (same g), in the fused passes of the step."""
+        check(self.lib.vp_kick(self.sim._ctx, float(tau), float(tau_next)), "vp_kick")
 
     def drift_yz(self, tau: float) -> None:
-        self.sim.sweep(2, tau)
-        self.sim.sweep(1, tau)
+        check(self.lib.vp_drift_yz(self.sim._ctx, float(tau)), "vp_drift_yz")
 
     def line_max_x(self) -> Tensor:
         out = torch.empty(self.f.shape[1:], dtype=self.f.dtype, device=self.f.device)
@@ -223,8 +224,11 @@ class LibrarySlab:
 class ShardedStep:
     """The split step over x slabs.  `slabs` are this process's slabs in x
     order (all of them with a LocalExchange, its own one with a
-    DistExchange); each provides kick, drift_yz, line_max_x, planes, drift_x,
-    density, field, set_accel, vmax_x, dx and the attributes x0, nx."""
+    DistExchange); each provides kick(tau[, tau_next]), drift_yz,
+    line_max_x, planes, drift_x, density, field, set_accel, vmax_x, dx and
+    the attributes x0, nx.  Within one call of step(n) the second half kick
+    of a step and the first of the next run together (they share g^{n+1}),
+    as in the single-context step."""
 
     def __init__(self, slabs: Sequence, exchange):
         self.slabs = list(slabs)
@@ -250,10 +254,11 @@ class ShardedStep:
         return G
 
     def step(self, nsteps: int = 1) -> float:
-        for _ in range(nsteps):
+        for n in range(nsteps):
             dt = self.dt
-            for s in self.slabs:
-                s.kick(0.5 * dt)
+            if n == 0:
+                for s in self.slabs:
+                    s.kick(0.5 * dt)                     # K1 of the first step
             for s in self.slabs:
                 s.drift_yz(dt)
             lmax = self.ex.allreduce_max([s.line_max_x() for s in self.slabs])
@@ -263,6 +268,9 @@ class ShardedStep:
                 s.drift_x(dt, lo, hi, G, m)
             self.dt = self._field()
             for s in self.slabs:
-                s.kick(0.5 * dt)
+                if n + 1 < nsteps:
+                    s.kick(0.5 * dt, 0.5 * self.dt)      # K2 of this step, K1 of the next
+                else:
+                    s.kick(0.5 * dt)                     # K2 of the last step
             self.t += dt
         return self.t

@@ -78,6 +78,42 @@ def test_slabs_equal_the_whole_box(nslabs, dtype, tol, fixed_dt):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("nslabs", [2, 4])
+def test_slabs_on_the_register_kernels(nslabs):
+    """FP32 slabs whose kicks run as the fused one-pass kick of 16^3 cubes
+    (K2 of a step and K1 of the next together) and whose z and y drifts run
+    as the fused drift (N_y = N_z = 32): the slabs' steps against the whole
+    box's vp_step and against the FP64 oracle."""
+    from paper_1206_6152_gb300.sharded import LibrarySlab, LocalExchange, ShardedStep
+    from paper_1206_6152_gb300.vlasov import VlasovPoisson, config_of
+    w = I.small_maxwell(n=(8, 32, 32), nv=(16, 16, 16), dtype="f32", amp=0.3, G=25.0)
+    w = w.replace(box_lo=(-0.5,) * 3, box_hi=(0.5,) * 3)
+    f0 = I.initial_condition(w)
+    nsteps = 3
+    fw = torch.from_numpy(f0).to(DEV, torch.float32)
+    with VlasovPoisson(config_of(w), fw) as sim:
+        t_whole = sim.step(nsteps, sync=True)
+    whole = fw.cpu().numpy().astype(np.float64)
+    fs = torch.from_numpy(f0).to(DEV, torch.float32)
+    nx = w.n[0] // nslabs
+    cfg = config_of(w)
+    slabs = [LibrarySlab(cfg, r * nx, fs[r * nx:(r + 1) * nx]) for r in range(nslabs)]
+    try:
+        t = ShardedStep(slabs, LocalExchange()).step(nsteps)
+        torch.cuda.synchronize()
+        got = fs.cpu().numpy().astype(np.float64)
+    finally:
+        for s in slabs:
+            s.close()
+    assert t == pytest.approx(t_whole, rel=1e-6)
+    assert np.abs(got - whole).sum() / np.abs(whole).sum() <= 1e-5
+    ref = O.Simulation(f0.astype(np.float64), O.Grid.of(w), O.Params.of(w))
+    ref.step(nsteps)
+    assert np.abs(got - ref.f).sum() / np.abs(ref.f).sum() <= 1e-5
+    assert got.min() >= 0.0
+
+
+@pytest.mark.gpu
 def test_slab_entry_points_check_their_arguments():
     from paper_1206_6152_gb300 import _lib
     from paper_1206_6152_gb300.sharded import LibrarySlab
@@ -99,6 +135,12 @@ def test_slab_entry_points_check_their_arguments():
         assert rc == -6
         rc = lib.vp_line_max_x(slab._fctx, ctypes.c_void_p(lm.data_ptr()))
         assert rc == -6
+        assert lib.vp_kick(slab._fctx, 0.01, 0.0) == -6
+        assert lib.vp_drift_yz(slab._fctx, 0.01) == -6
+        # non-finite durations are refused
+        assert lib.vp_kick(slab.sim._ctx, math.nan, 0.0) == -5
+        assert lib.vp_kick(slab.sim._ctx, 0.01, math.inf) == -5
+        assert lib.vp_drift_yz(slab.sim._ctx, math.nan) == -5
         # its field is the oracle's
         rho = slab.density()
         rho_all = torch.cat([rho, rho])

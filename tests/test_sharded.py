@@ -40,9 +40,10 @@ class OracleSlab:
         self.f = np.array(f0[x0:x0 + nx], dtype=np.float64)
         self.g = None
 
-    def kick(self, tau):
-        for a in range(3):
-            O.sweep(self.f, 3 + a, self.g[a], tau, self.grid.dv[a], False)
+    def kick(self, tau, tau_next=0.0):
+        for t in (tau, tau_next) if tau_next else (tau,):
+            for a in range(3):
+                O.sweep(self.f, 3 + a, self.g[a], t, self.grid.dv[a], False)
 
     def drift_yz(self, tau):
         for a in (2, 1):
