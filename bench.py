@@ -690,7 +690,10 @@ def time_adjoint(args, name, dev, stream):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     fwd = e0.elapsed_time(e1) / k
-    f_start = f.clone()
+    # the step-start state is the context's own f, which the adjoint step
+    # leaves unchanged, as in the checkpointed trajectory (adjoint.py): the
+    # memory a copy would take goes to the adjoint's scratch states
+    f_start = f
     g_start = sim.field()[2]
     lam_f = torch.zeros_like(f)
     lam_g = torch.zeros_like(g_start)
@@ -709,8 +712,9 @@ def time_adjoint(args, name, dev, stream):
     return {"workload": w.name, "forward_ms_per_step": round(fwd, 3),
             "adjoint_ms_per_step": round(adj, 3), "ratio": round(adj / fwd, 3),
             "note": "adjoint step = replay of its forward step keeping the sweep inputs it cannot "
-                    "recompute locally + 9 adjoint sweeps + field adjoint; the recompute of the "
-                    "step-start states from the checkpoints is not included"}
+                    "recompute locally + 9 adjoint sweeps + field adjoint; the step-start state is "
+                    "the context's own f; the recompute of the step-start states from the "
+                    "checkpoints is not included"}
 
 
 def run_reference(args, ranks: Ranks):

@@ -175,9 +175,9 @@ int vp_debug_fail_alloc(int k);
  * sweeps of the replayed step that its adjoint reads (at most eight states
  * of f's size; six for FP32 velocity cubes of edge 16 or 32 with fused y+z
  * drifts) or, where they do not fit or vp_set_adjoint_states asks for it,
- * two states with which the inputs are recomputed from f_start in four
- * partial replays (about 2.5 times the passes over f); VP_ERR_OOM if even
- * two do not fit.
+ * three or two states with which the inputs are recomputed from f_start in
+ * partial replays (12 or 15 passes over f against the forward step's
+ * six); VP_ERR_OOM if even two do not fit.
  *   f_start: the step-start f^n (device, same layout/dtype as f; read only)
  *   g_start: the step-start acceleration g^n (3 N^p doubles, device)
  *   lambda_f: in: cotangent of f^{n+1}; out: cotangent of f^n (device,
@@ -187,8 +187,9 @@ int vp_debug_fail_alloc(int k);
  * The context's own f is not modified; the context's scratch is used to
  * replay the forward step. */
 /* Scratch policy of vp_adjoint_step (not in the paper): 0 automatic (the
- * kept sweep inputs if they fit, else two states), 1 two states
- * (recompute), 2 the kept sweep inputs.  Frees the scratch held so far;
+ * kept sweep inputs if they fit, else three states, else two), 1 two
+ * states (the sweep inputs recomputed), 2 the kept sweep inputs, 3 three
+ * states (fewer recomputed than with two).  Frees the scratch held so far;
  * VP_ERR_ARG for another mode. */
 int vp_set_adjoint_states(vp_ctx *ctx, int mode);
 

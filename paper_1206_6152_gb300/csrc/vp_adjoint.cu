@@ -639,6 +639,8 @@ bool alloc_adjoint_states(vp_ctx *c, int n, const bool *want, const int *alias)
     return true;
 }
 
+// Modes: 0 the nine-slot mode if it fits, else three states, else two; 1
+// two states; 2 the nine-slot mode; 3 three states.
 // The nine-slot mode keeps S1..S8 (S[k]: the input of sweep k of the step;
 // S0 = f^n is the caller's): only the slots the step's path reads — with
 // the register kick adjoint S2 and S8 are scratch for the fix-up of
@@ -661,7 +663,7 @@ int ensure_adjoint_scratch(vp_ctx *c)
             return VP_ERR_OOM;
         }
     }
-    if (c->adj_mode != 1) {
+    if (c->adj_mode == 0 || c->adj_mode == 2) {
         const bool reg = vp_kick_adjoint3_ok(c);
         const bool yz = vp_drift_alpha_bound(c, c->cfg.dt_fixed) < 1.0 && vp_drift_adjoint_yz_ok(c);
         bool want[9];
@@ -675,9 +677,13 @@ int ensure_adjoint_scratch(vp_ctx *c)
         if (alloc_adjoint_states(c, 9, want, alias)) return VP_OK;
     }
     if (c->adj_mode == 2) return VP_ERR_OOM;
-    const bool two[2] = {true, true};
-    const int id[2] = {0, 1};
-    return alloc_adjoint_states(c, 2, two, id) ? VP_OK : VP_ERR_OOM;
+    const bool all[3] = {true, true, true};
+    const int id[3] = {0, 1, 2};
+    if (c->adj_mode == 0 || c->adj_mode == 3) {
+        if (alloc_adjoint_states(c, 3, all, id)) return VP_OK;
+        if (c->adj_mode == 3) return VP_ERR_OOM;
+    }
+    return alloc_adjoint_states(c, 2, all, id) ? VP_OK : VP_ERR_OOM;
 }
 
 // scalar on the device used as the replay's tau
@@ -842,7 +848,7 @@ int vp_functional(vp_ctx *c, int kind, const double *target, void *lambda_f, dou
 
 int vp_set_adjoint_states(vp_ctx *c, int mode)
 {
-    if (!c || mode < 0 || mode > 2) return VP_ERR_ARG;
+    if (!c || mode < 0 || mode > 3) return VP_ERR_ARG;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
         cudaGetLastError();
         return VP_ERR_CUDA;
@@ -924,6 +930,54 @@ int adjoint_step_two_states(vp_ctx *c, const void *S0, void *lambda_f, double *l
     return VP_OK;
 }
 
+// The adjoint step with three scratch states X, Y, Z (the replays move 96
+// bytes per cell against 120 with two states):
+//   S0 -> S3 (X) -> S4 (Y) -> S5 (Z) -> S6 (Y) [g^{n+1}];  S8 from S6 (vx
+//   and vy in one pass, X): vz;  S7 from S6 (X): vy;  S6: vx;  field
+//   S5: x
+//   S0 -> S3 (X) -> S4 (Y): y;  S3: z               (fused y+z: S3 alone)
+//   S2 from S0 (vx and vy, X): vz;  S1 from S0 (X): vy;  S0: vx
+int adjoint_step_three_states(vp_ctx *c, const void *S0, void *lambda_f, double *lambda_g,
+                              const void *k1, const double *tau_ptr, double dt, double amax)
+{
+    void *X = c->adj_states[0], *Y = c->adj_states[1], *Z = c->adj_states[2];
+    const double tau = 0.5 * dt;
+    const bool yz = amax < 1.0 && vp_drift_adjoint_yz_ok(c);
+    // replay to S6 keeping S5; the density of S6 gives g^{n+1}
+    TRY(replay_kick(c, S0, X, k1, 3));                                            // X = S3
+    VP_CUDA_TRY(launch_sweep_into(c, X, Y, 2, c->coef_drift, amax));              // Y = S4
+    VP_CUDA_TRY(launch_sweep_into(c, Y, Z, 1, c->coef_drift, amax));              // Z = S5
+    VP_CUDA_TRY(launch_sweep_into(c, Z, Y, 0, c->coef_drift, amax));              // Y = S6
+    VP_CUDA_TRY(launch_density(c, Y, c->rho2));
+    VP_CUDA_TRY(launch_field_solve(c, c->rho2, c->adj_g));
+    VP_CUDA_TRY(launch_coef_kick(c, c->adj_g, tau_ptr, 0.5, c->coef_kick2));
+    // K2 reversed with S6 in Y
+    TRY(replay_kick(c, Y, X, c->coef_kick2, 2));                                  // X = S8
+    VP_CUDA_TRY(launch_kick_adjoint(c, X, lambda_f, 2, c->coef_kick2, tau, lambda_g));
+    VP_CUDA_TRY(launch_sweep_into(c, Y, X, 3, c->coef_kick2, amax));              // X = S7
+    VP_CUDA_TRY(launch_kick_adjoint(c, X, lambda_f, 1, c->coef_kick2, tau, lambda_g));
+    VP_CUDA_TRY(launch_kick_adjoint(c, Y, lambda_f, 0, c->coef_kick2, tau, lambda_g));
+    VP_CUDA_TRY(launch_field_adjoint(c, lambda_g, lambda_f, true));
+    // the drifts reversed: S5 is in Z; S3 and S4 replayed again
+    VP_CUDA_TRY(launch_drift_adjoint(c, Z, lambda_f, 0, c->coef_drift, c->rho2));
+    TRY(replay_kick(c, S0, X, k1, 3));                                            // X = S3
+    if (yz) {
+        VP_CUDA_TRY(launch_drift_adjoint_yz(c, X, lambda_f, c->coef_drift));
+    } else {
+        VP_CUDA_TRY(launch_sweep_into(c, X, Y, 2, c->coef_drift, amax));          // Y = S4
+        VP_CUDA_TRY(launch_drift_adjoint(c, Y, lambda_f, 1, c->coef_drift, nullptr));
+        VP_CUDA_TRY(launch_drift_adjoint(c, X, lambda_f, 2, c->coef_drift, nullptr));
+    }
+    // K1 reversed
+    VP_CUDA_TRY(cudaMemsetAsync(lambda_g, 0, sizeof(double) * 3 * c->np, c->stream));
+    TRY(replay_kick(c, S0, X, k1, 2));                                            // X = S2
+    VP_CUDA_TRY(launch_kick_adjoint(c, X, lambda_f, 2, k1, tau, lambda_g));
+    VP_CUDA_TRY(launch_sweep_into(c, S0, X, 3, k1, amax));                        // X = S1
+    VP_CUDA_TRY(launch_kick_adjoint(c, X, lambda_f, 1, k1, tau, lambda_g));
+    VP_CUDA_TRY(launch_kick_adjoint(c, S0, lambda_f, 0, k1, tau, lambda_g));
+    return VP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -949,8 +1003,10 @@ int vp_adjoint_step(vp_ctx *c, const void *f_start, const double *g_start, void 
     VP_CUDA_TRY(launch_coef_drift(c, tau_ptr, 1.0, c->coef_drift));
     const double amax = vp_drift_alpha_bound(c, dt);
     const void *S0 = f_start;     // S[k]: input of sweep k of the step (S[0] = f^n)
-    if (c->adj_nstates == 2) {
-        const int r = adjoint_step_two_states(c, S0, lambda_f, lambda_g, k1, tau_ptr, dt, amax);
+    if (c->adj_nstates == 2 || c->adj_nstates == 3) {
+        const int r = c->adj_nstates == 2
+                          ? adjoint_step_two_states(c, S0, lambda_f, lambda_g, k1, tau_ptr, dt, amax)
+                          : adjoint_step_three_states(c, S0, lambda_f, lambda_g, k1, tau_ptr, dt, amax);
         VP_CUDA_TRY(cudaMemcpyAsync(&c->sc->lost, &c->sc->pad[1], sizeof(double),
                                     cudaMemcpyDeviceToDevice, c->stream));
         return r;

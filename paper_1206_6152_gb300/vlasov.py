@@ -207,7 +207,8 @@ class VlasovPoisson:
 
     def set_adjoint_states(self, mode: int) -> None:
         """Scratch policy of adjoint_step: 0 automatic, 1 two states
-        (recompute), 2 the kept sweep inputs (at most eight states)."""
+        (recompute), 2 the kept sweep inputs (at most eight states), 3 three
+        states."""
         check(self.lib.vp_set_adjoint_states(self._ctx, int(mode)), "vp_set_adjoint_states")
 
     def sweep_adjoint(self, axis: int, tau: float, f_in: torch.Tensor, lam: torch.Tensor,

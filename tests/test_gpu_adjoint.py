@@ -112,7 +112,7 @@ def test_register_adjoint_sweeps_match_oracle(dtype, shape, space_bc):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("states", [0, 1])
+@pytest.mark.parametrize("states", [0, 1, 3])
 @pytest.mark.parametrize("bc", ["periodic", "isolated"])
 def test_adjoint_step_matches_oracle(bc, states):
     w = I.small_maxwell(n=(6, 5, 4), nv=(8, 7, 6), dtype="f64", amp=0.2, G=20.0)
@@ -124,7 +124,7 @@ def test_adjoint_step_matches_oracle(bc, states):
     rng = np.random.default_rng(3)
     f0 = I.initial_condition(w) * (1 + 0.2 * rng.random(w.shape))
     sim, f = gpu_sim(w, f0)
-    sim.set_adjoint_states(states)           # 1: inputs recomputed with two states
+    sim.set_adjoint_states(states)           # 1, 3: inputs recomputed with two or three states
     g0 = sim.field()[2]
     lam_f = torch.from_numpy(rng.normal(size=w.shape)).to(DEV)
     lam_g = torch.from_numpy(rng.normal(size=(3,) + w.n)).to(DEV)
@@ -142,7 +142,8 @@ def test_adjoint_step_matches_oracle(bc, states):
 @pytest.mark.gpu
 @pytest.mark.parametrize("G,n,states", [(20.0, (16, 2, 2), 0), (200.0, (16, 2, 2), 0),
                                         (20.0, (2, 16, 16), 0), (20.0, (16, 2, 2), 1),
-                                        (2000.0, (2, 16, 16), 1)])
+                                        (2000.0, (2, 16, 16), 1), (20.0, (16, 2, 2), 3),
+                                        (20.0, (2, 16, 16), 3)])
 def test_adjoint_step_fp32_register_kernels_match_oracle(G, n, states):
     """FP32 adjoint step on grids served by the packed kernels against the
     FP64 oracle's adjoint step: x lines of 16 with the density broadcast
@@ -178,11 +179,11 @@ def test_adjoint_step_fp32_register_kernels_match_oracle(G, n, states):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("states", [0, 1])
+@pytest.mark.parametrize("states", [0, 1, 3])
 def test_adjoint_step_48_cubes_match_oracle(states):
     """FP32 adjoint step with 48^3 velocity cubes (out-of-place replay kicks,
     per-axis register adjoints over any number of cubes) against the FP64
-    oracle, with nine kept states and with two."""
+    oracle, with nine kept states, with two and with three."""
     w = I.large_c5().replace(n=(2, 2, 2), box_lo=(-0.5,) * 3, box_hi=(0.5,) * 3, G=40.0,
                              dt_fixed=0.01)
     grid = O.Grid.of(w)
