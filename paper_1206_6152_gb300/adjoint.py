@@ -62,8 +62,8 @@ class _Trajectory(torch.autograd.Function):
         fbytes = f.numel() * f.element_size()
         nck = (nsteps + every - 1) // every
         # checkpoints on the device if they leave room for the backward's
-        # cotangent, the adjoint's two scratch states and one segment state
-        ck_dev = _free_bytes(f.device) > (nck + 4) * fbytes
+        # cotangent, the adjoint's three scratch states and one segment state
+        ck_dev = _free_bytes(f.device) > (nck + 5) * fbytes
         with torch.no_grad():
             f.copy_(f0)
             sim.refresh_field()

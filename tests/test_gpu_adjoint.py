@@ -335,8 +335,8 @@ def _fill_mode_f0(w, amps, out):
 def test_jeans48_modes8_trajectory_gradient_matches_fd():
     """The 48^3 x 48^3 FP32 forward+adjoint workload at a reduced step count:
     20 steps from f0(A) with checkpoints every 10 (two checkpoints; they go
-    to pinned host memory because the device cannot hold them beside f, the
-    cotangent and the adjoint's two scratch states) and every step-start
+    to pinned host memory because the device cannot hold them beside f, f0,
+    the cotangent and the adjoint's scratch states, two here) and every step-start
     state recomputed from its checkpoint.  The gradient of the final field
     energy with respect to the eight mode amplitudes, dJ/dA_m = rho_bar
     sum_x cos(k_m.x + th_m) sum_v lambda_0(x, v) M(v) with lambda_0 = dJ/df0
