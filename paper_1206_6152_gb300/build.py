@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["vp_api.cu", "vp_sweep.cu", "vp_sweep_fast.cu", "vp_kick_big.cu", "vp_field.cu",
-           "vp_adjoint.cu", "vp_adjoint_fast.cu", "vp_noalloc.cu", "vp_shard.cu"]
+           "vp_adjoint.cu", "vp_adjoint_fast.cu", "vp_noalloc.cu", "vp_shard.cu", "vp_sweep_f64.cu"]
 
 
 def nvcc() -> str:

@@ -8,6 +8,23 @@
 #include "vp_internal.cuh"
 
 // ---------------------------------------------------------------------------
+// FP64 minimum and maximum on the integer pipes: GB300 issues FP64
+// instructions at a small fraction of its integer rate, and a comparison of
+// two doubles is exact on a key of their bits that orders every non-NaN
+// double as its value (-0 below +0).  vmin/vmax: these for double, the FP32
+// instructions for float.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long dkey(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double vmin(double a, double b) { return dkey(b) < dkey(a) ? b : a; }
+__device__ __forceinline__ double vmax(double a, double b) { return dkey(b) > dkey(a) ? b : a; }
+__device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
+
+// ---------------------------------------------------------------------------
 // PFC partial flux of cell j (Sec. 2.1): the integral of the third-order
 // reconstruction over the fraction beta of cell j that crosses its downwind
 // face, in units of the cell average.  The slope corrector of Filbet,
@@ -25,10 +42,10 @@ __device__ __forceinline__ T pfc_flux(T fm, T f0, T fp, T finf, T c0, T c1, T c2
 {
     const T a = f0 + f0;
     const T b = (finf - f0) * T(2);
-    const T ep = fmin(fmax(fp - f0, -b), a);
-    const T em = fmin(fmax(f0 - fm, -a), b);
+    const T ep = vmin(vmax(fp - f0, -b), a);
+    const T em = vmin(vmax(f0 - fm, -a), b);
     T phi = c0 * f0 + c1 * ep + c2 * em;
-    return fmin(fmax(phi, T(0)), f0);
+    return vmin(vmax(phi, T(0)), f0);
 }
 
 // ---------------------------------------------------------------------------

@@ -71,7 +71,7 @@ __device__ __noinline__ T kick_line_shifted(T *L, int st, int n, const LineCoef<
     const int s = cf.code >> 1, neg = cf.code & 1;
     const T c0 = cf.c0, c1 = cf.c1, c2 = cf.c2;
     T finf = T(0);
-    for (int j = 0; j < n; ++j) finf = fmax(finf, L[j * st]);
+    for (int j = 0; j < n; ++j) finf = vmax(finf, L[j * st]);
     T lost = T(0);
     for (int j = (n - s > 0 ? n - s : 0); j < n; ++j) lost += L[upos(j, n, neg) * st];
     const int jtop = n - 1 - s;

@@ -145,6 +145,11 @@ cudaError_t launch_kick_big(vp_ctx *c, void *f, const void *ca, const void *cb, 
                             int first_axis, void *fo = nullptr);
 cudaError_t launch_kick_big3(vp_ctx *c, float *f, const LineCoef<float> *ca,
                              const LineCoef<float> *cb, int nsweeps, int first_axis, float *fo);
+// FP64 cubes of edge 16 or 32: one launch per sweep, one line per thread in
+// registers (vp_sweep_f64.cu); fo: output array (nullptr: in place)
+int vp_kick_f64_ok(const vp_ctx *c);
+cudaError_t launch_kick_f64(vp_ctx *c, void *f, const void *ca, const void *cb, int nsweeps,
+                            int first_axis, void *fo);
 // fused z then y drift of the whole grid (FP32, N_y = N_z in {16, 32}; in
 // place when fo == f)
 int vp_drift_yz_ok(const vp_ctx *c);

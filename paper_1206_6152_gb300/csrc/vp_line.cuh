@@ -23,6 +23,8 @@
 
 #include <cuda_runtime.h>
 
+#include "vp_device.cuh"
+
 namespace vpline {
 
 // ---------------------------------------------------------------------------
@@ -38,7 +40,12 @@ __device__ __forceinline__ float fmasat(float a, float b, float c)
 }
 __device__ __forceinline__ double fmasat(double a, double b, double c)
 {
-    return fmin(fmax(::fma(a, b, c), 0.0), 1.0);   // NaN -> 0, as the f32 .sat form
+    // the clamp to [0, 1] on the bits (the integer pipes, not the FP64
+    // one): a non-negative double orders like its bit pattern; u <= 0 and
+    // NaN give 0, as the f32 .sat form
+    const double u = ::fma(a, b, c);
+    const long long k = __double_as_longlong(u);
+    return k <= 0 ? 0.0 : (k >= 0x3ff0000000000000LL ? (k > 0x7ff0000000000000LL ? 0.0 : 1.0) : u);
 }
 __device__ __forceinline__ float max3(float a, float b, float c)
 {
@@ -46,7 +53,7 @@ __device__ __forceinline__ float max3(float a, float b, float c)
     asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
     return r;
 }
-__device__ __forceinline__ double max3(double a, double b, double c) { return fmax(a, fmax(b, c)); }
+__device__ __forceinline__ double max3(double a, double b, double c) { return ::vmax(a, ::vmax(b, c)); }
 
 template <typename V>
 struct VOps;
@@ -99,7 +106,7 @@ struct VOps<double> {
     __device__ __forceinline__ static double add(double a, double b) { return a + b; }
     __device__ __forceinline__ static double sub(double a, double b) { return a - b; }
     __device__ __forceinline__ static double fsat(double a, double b, double c) { return fmasat(a, b, c); }
-    __device__ __forceinline__ static double vmin(double a, double b) { return fmin(a, b); }
+    __device__ __forceinline__ static double vmin(double a, double b) { return ::vmin(a, b); }
     __device__ __forceinline__ static double zero() { return 0.0; }
 };
 
@@ -123,7 +130,7 @@ __device__ __forceinline__ double line_max(const double (&x)[N])
 {
     double m = 0.0;
 #pragma unroll
-    for (int j = 0; j < N; ++j) m = fmax(m, x[j]);
+    for (int j = 0; j < N; ++j) m = ::vmax(m, x[j]);
     return m;
 }
 // tree of 3-input maxima (short dependency chain)

@@ -30,7 +30,7 @@ __global__ void k_line_max_x(const T *__restrict__ f, T *__restrict__ out, long 
     for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < nl;
          l += (long long)gridDim.x * blockDim.x) {
         T m = T(0);
-        for (int i = 0; i < nx; ++i) m = fmax(m, f[(long long)i * nl + l]);
+        for (int i = 0; i < nx; ++i) m = vmax(m, f[(long long)i * nl + l]);
         out[l] = m;
     }
 }

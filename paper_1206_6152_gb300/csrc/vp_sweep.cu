@@ -39,7 +39,7 @@ __device__ T kick_line(T *L, int st, int n, const LineCoef<T> cf)
     const int s = cf.code >> 1, neg = cf.code & 1;
     const T c0 = cf.c0, c1 = cf.c1, c2 = cf.c2;
     T finf = T(0);
-    for (int j = 0; j < n; ++j) finf = fmax(finf, L[j * st]);
+    for (int j = 0; j < n; ++j) finf = vmax(finf, L[j * st]);
     if (s == 0) {
         T fm = T(0), f0 = L[upos(0, n, neg) * st], phim = T(0);
         for (int i = 0; i < n; ++i) {
@@ -234,7 +234,7 @@ __device__ T drift_line(const T *L, int st, int n, const LineCoef<T> cf, T *out,
     const int s = cf.code >> 1;
     const T c0 = cf.c0, c1 = cf.c1, c2 = cf.c2;
     T finf = T(0);
-    for (int j = 0; j < n; ++j) finf = fmax(finf, L[j * st]);
+    for (int j = 0; j < n; ++j) finf = vmax(finf, L[j * st]);
     if (PERIODIC) {
         const int sm = s % n;
         T fm = L[upos(n - 1, n, neg) * st], f0 = L[upos(0, n, neg) * st];
@@ -641,6 +641,7 @@ cudaError_t launch_kick(vp_ctx *c, void *f, const void *coef_a, const void *coef
 {
     if (vp_kick_fast_ok(c)) return launch_kick_fast(c, f, coef_a, coef_b, nsweeps, first_axis);
     if (vp_kick_big_ok(c)) return launch_kick_big(c, f, coef_a, coef_b, nsweeps, first_axis);
+    if (vp_kick_f64_ok(c)) return launch_kick_f64(c, f, coef_a, coef_b, nsweeps, first_axis, nullptr);
     if (c->isdouble)
         return launch_kick_dispatch<double>(c, (double *)f, (const LineCoef<double> *)coef_a,
                                             (const LineCoef<double> *)coef_b, nsweeps,
@@ -656,6 +657,8 @@ cudaError_t launch_sweep_into(vp_ctx *c, const void *src, void *dst, int axis, c
         return launch_kick_fast(c, const_cast<void *>(src), coef, nullptr, 1, axis - 3, dst);
     if (axis >= 3 && vp_kick_big_ok(c))
         return launch_kick_big(c, const_cast<void *>(src), coef, nullptr, 1, axis - 3, dst);
+    if (axis >= 3 && vp_kick_f64_ok(c))
+        return launch_kick_f64(c, const_cast<void *>(src), coef, nullptr, 1, axis - 3, dst);
     if (axis < 3 && vp_drift_fast_ok(c, axis) && drift_alpha_bound < 1.0)
         return launch_drift_fast(c, const_cast<void *>(src), axis, coef, nullptr, dst);
     cudaError_t e = cudaMemcpyAsync(dst, src, (size_t)c->ncells * c->esize,

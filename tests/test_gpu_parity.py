@@ -548,6 +548,36 @@ def test_split_steps_32_cubes(whole_cell):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("whole_cell", [False, True])
+@pytest.mark.parametrize("nv", [16, 32])
+def test_split_steps_fp64_register_lines(nv, whole_cell):
+    """FP64 split steps on the register-line FP64 kernels: velocity cubes of
+    16^3 and 32^3 swept one line per thread, and lines of 32 along x (the
+    FP64 register-line drift), against the FP64 oracle; with whole_cell, a
+    fixed dt under which the kick moves half of the cubes by more than one
+    cell (their lines take the generic in-place routine)."""
+    w = I.small_maxwell(n=(32, 2, 2), nv=(nv,) * 3, dtype="f64", amp=0.3, G=25.0)
+    w = w.replace(box_lo=(-0.5, -0.05, -0.05), box_hi=(0.5, 0.05, 0.05))
+    f0 = I.initial_condition(w)
+    grid = O.Grid.of(w)
+    if whole_cell:
+        g0 = O.force(O.poisson(O.density(f0, grid), grid, w.G, "periodic"), grid, "periodic")
+        amax = max(np.abs(g0[a]).max() / grid.dv[a] for a in range(3))
+        w = w.replace(dt_fixed=2 * 1.6 / amax)
+    sim, f = gpu_sim(w, f0)
+    t = sim.step(3, sync=True)
+    got = f.cpu().numpy()
+    e = sim.energy()
+    ref = O.Simulation(f0, grid, O.Params.of(w))
+    ref.step(3)
+    assert abs(t - ref.t) <= 1e-13 * ref.t
+    assert rel_l1(got, ref.f) <= 1e-12
+    assert got.min() >= 0.0
+    assert e["M_out"] == pytest.approx(ref.energy()[4], rel=1e-9, abs=1e-12 * ref.energy()[0])
+    sim.close()
+
+
+@pytest.mark.gpu
 @pytest.mark.slow
 def test_jeans48_full_size_sweeps_and_steps():
     """The 48^3 x 48^3 FP32 box (49 GB of f) in the benchmark's launch
