@@ -896,7 +896,7 @@ int vp_drift_fast_ok(const vp_ctx *c, int axis)
     const int n = c->n[axis];
     if (!(n == 16 || n == 32 || n == 48 || n == 64)) return 0;
     if (!c->isdouble && (c->nvc % 2 != 0)) return 0;
-    if (c->isdouble && n > 16) return 0;
+    if (c->isdouble && n > 32) return 0;
     return 1;
 }
 
@@ -923,6 +923,7 @@ cudaError_t launch_drift_fast(vp_ctx *c, void *f, int axis, const void *coef, do
     const int np = rho_part ? vp_rho_parts(c) : 0;
     if (c->isdouble) {
         const LineCoef<double> *cf = (const LineCoef<double> *)coef + (size_t)axis * c->maxnv;
+        if (n == 32) return drift_fast_n<double, 32>(c, (double *)f, axis, cf, rho_part, np, (double *)fo);
         return drift_fast_n<double, 16>(c, (double *)f, axis, cf, rho_part, np, (double *)fo);
     }
     const LineCoef<float> *cf = (const LineCoef<float> *)coef + (size_t)axis * c->maxnv;
