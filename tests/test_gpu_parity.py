@@ -567,11 +567,14 @@ def test_split_steps_fp64_register_lines(nv, whole_cell):
     sim, f = gpu_sim(w, f0)
     t = sim.step(3, sync=True)
     got = f.cpu().numpy()
+    rho_g = sim.field()[0].cpu().numpy()
     e = sim.energy()
     ref = O.Simulation(f0, grid, O.Params.of(w))
     ref.step(3)
     assert abs(t - ref.t) <= 1e-13 * ref.t
     assert rel_l1(got, ref.f) <= 1e-12
+    # the density of the stepped f (the field solve's input)
+    assert np.abs(rho_g - ref.rho).max() <= 1e-12 * ref.rho.max()
     assert got.min() >= 0.0
     assert e["M_out"] == pytest.approx(ref.energy()[4], rel=1e-9, abs=1e-12 * ref.energy()[0])
     sim.close()
