@@ -91,10 +91,7 @@ struct Acc<double> {
     __device__ __forceinline__ void add(double x)
     {
         const double t = s + x;
-        // |s| >= |x| on the bits without the sign (the integer pipes)
-        const long long ms = __double_as_longlong(s) & 0x7fffffffffffffffLL;
-        const long long mx = __double_as_longlong(x) & 0x7fffffffffffffffLL;
-        if (ms >= mx)
+        if (fabs(s) >= fabs(x))
             c += (s - t) + x;
         else
             c += (x - t) + s;

@@ -388,20 +388,6 @@ __global__ void __launch_bounds__(256) k_density(const T *__restrict__ f, long l
             a.merge(b);
             c2.merge(d);
             a.merge(c2);
-        } else if (sizeof(T) == 8 && (nvc & 3) == 0) {
-            // the same for doubles: four sums over two 16-byte loads
-            Acc<T> b, c2, d;
-            const double2 *q2 = reinterpret_cast<const double2 *>(q);
-            for (int e = threadIdx.x; e < nvc / 4; e += blockDim.x) {
-                const double2 v = q2[2 * e], u = q2[2 * e + 1];
-                a.add((T)v.x);
-                b.add((T)v.y);
-                c2.add((T)u.x);
-                d.add((T)u.y);
-            }
-            a.merge(b);
-            c2.merge(d);
-            a.merge(c2);
         } else {
             for (int e = threadIdx.x; e < nvc; e += blockDim.x) a.add(q[e]);
         }
