@@ -113,3 +113,35 @@ def test_cores_are_the_oracles_openmp_threads():
     from oracle import vp_oracle as O
     n = bench.oracle_threads()
     assert n == O.threads() and 1 <= n <= (os.cpu_count() or n)
+
+
+@pytest.mark.parametrize("big_kick,fused_yz", [(True, False), (True, True), (False, False),
+                                               (False, True)])
+def test_roofline_passes_follow_the_profiled_step(big_kick, fused_yz, monkeypatch):
+    """The roofline's passes are the step's own: the three slab passes of
+    the 48^3 kick or the one-pass kick, the fused z+y drift where the z slot
+    holds both drifts (the y slot then empty) or the two separate drifts, and
+    the x drift; the dominant kernel is the longest pass, the step fraction
+    counts one read and one write of f per pass."""
+    monkeypatch.setattr(bench, "load_peaks", lambda: (1000.0, "measured"))
+    monkeypatch.setattr(bench, "load_traffic", lambda key: None)
+    w = I.WORKLOADS["jeans48_modes8"]() if big_kick else I.WORKLOADS["jeans32_f32"]()
+    avg = {"kick6": 30.0, "drift_z": 10.0, "drift_y": 0.001 if fused_yz else 9.0, "drift_x": 8.0,
+           "density": 0.0, "field": 0.3, "tables": 0.2, "step": 0.0,
+           "kick_a": 12.0 if big_kick else 0.0, "kick_b": 9.5 if big_kick else 0.0,
+           "kick_c": 9.0 if big_kick else 0.0}
+    if not big_kick:
+        avg["kick6"] = 11.0
+    kick = ["kick_a", "kick_b", "kick_c"] if big_kick else ["kick6"]
+    drift = ["drift_yz", "drift_x"] if fused_yz else ["drift_z", "drift_y", "drift_x"]
+    avg["step"] = sum(avg[k] for k in kick) + sum(avg.get(k, avg["drift_z"]) for k in drift) + 0.5
+    r = bench.roofline_of(w, avg, 4)
+    assert list(r["passes"]) == kick + drift
+    longest = "kick_a" if big_kick else "kick6"
+    assert r["pass"] == longest
+    bytes_rw = 2 * w.cells * 4
+    assert r["achieved"] == pytest.approx(bytes_rw / (avg[longest] / 1e3) / 1e9, rel=1e-3)
+    assert r["step_bytes_algorithmic"] == len(kick + drift) * bytes_rw
+    assert r["step_hbm_frac"] == pytest.approx(
+        len(kick + drift) * bytes_rw / (avg["step"] / 1e3) / 1e9 / 1000.0, rel=1e-3)
+
